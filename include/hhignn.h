@@ -1,0 +1,187 @@
+/*
+ * hhignn.h -- C-ABI of libhhignn.so: the H-matrix mobility product of
+ * H-HIGNN (arXiv 2505.08174) on one NVIDIA B300 (sm_103a).
+ *
+ * The library computes particle velocities
+ *
+ *     U = alpha_1 F + M_H F                                   (Eq. 6)
+ *
+ * where alpha_1 = I / (6 pi mu a) is the single-body mobility (Section 2.2,
+ * Eq. 2) and M_H is the hierarchical-matrix approximation (Section 3) of the
+ * dense two-body matrix M^(t,2) whose 3x3 entries are
+ *
+ *     M_ij = S(MLP([r/|r|, a/|r|])) / |r|,   r = x_i - x_j     (Eq. 4)
+ *
+ * with S(o) = [[o0,o3,o4],[o3,o1,o5],[o4,o5,o2]] (or the closed-form
+ * Rotne-Prager-Yamakawa tensor when kernel = HH_RPY).  M_H is built from a
+ * cluster tree (Definition 1), the admissibility partition (Eq. 7,
+ * Algorithm 1), and block adaptive cross approximation on admissible blocks
+ * (Algorithm 2, Eqs. 8-10); inadmissible blocks are evaluated densely.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named *_dev are device pointers owned by the caller; the
+ *    library never frees them.  Opaque objects (hh_ctx, hh_tree, hh_blocks,
+ *    hh_hmat) are owned by the library and released with the matching
+ *    *_free / hh_destroy call.  An hh_blocks must not outlive its hh_tree,
+ *    nor an hh_hmat its hh_blocks.
+ *  - X, F, U, gU, gF, gX are [N, 3] row-major FP64.  theta is float32,
+ *    packed per layer as W [out, in] row-major followed by b [out], layers
+ *    4 -> w -> w -> w -> 6.
+ *  - stream is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued asynchronously; calls that must read a size back from the
+ *    GPU synchronise the stream internally (stated per call).
+ *  - Every call returns hh_status.  On an error the outputs are unspecified
+ *    and hh_last_error() returns a message.  HH_WARN_RANK_CAP is a warning:
+ *    the outputs are valid.
+ *  - The library is single-device: every object belongs to the device the
+ *    context was created on; calls must be made with that device current.
+ *  - The library allocates its temporaries with cudaMallocAsync on the
+ *    call's stream from the device's default memory pool.
+ */
+#ifndef HHIGNN_H
+#define HHIGNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hh_ctx hh_ctx;
+typedef struct hh_tree hh_tree;
+typedef struct hh_blocks hh_blocks;
+typedef struct hh_hmat hh_hmat;
+
+typedef enum {
+    HH_OK = 0,
+    HH_ERR_ARG = 1,       /* invalid argument or unsupported combination     */
+    HH_ERR_CUDA = 2,      /* a CUDA runtime call or kernel launch failed      */
+    HH_ERR_OOM = 3,       /* device allocation failed                         */
+    HH_ERR_TIMEOUT = 4,   /* a bounded device wait gave up                    */
+    HH_ERR_NUMERIC = 5,   /* NaN/Inf input or coincident particles            */
+    HH_WARN_RANK_CAP = 6  /* >= 1 admissible block stopped at max_rank        */
+} hh_status;
+
+enum { HH_FP64 = 0, HH_FP32 = 1, HH_BF16 = 2 };   /* hh_params.precision */
+enum { HH_MLP = 0, HH_RPY = 1 };                  /* hh_params.kernel    */
+
+/* Parameters of one H-matrix build (Section 3 and Section 4 notation). */
+typedef struct {
+    int32_t leaf_size;   /* C_leaf: a cluster is a leaf iff |tau| < C_leaf (Def. 1); 2..129 */
+    double eta;          /* admissibility parameter of Eq. 7 (> 0)                          */
+    double eps;          /* zeta, the ACA tolerance of Eq. 10                               */
+    int32_t max_rank;    /* N_max^ite: cap on the ACA rank per block (Section 3.3), 1..64   */
+    int32_t precision;   /* HH_FP64 | HH_FP32 | HH_BF16                                     */
+    int32_t kernel;      /* HH_MLP | HH_RPY                                                 */
+    double radius;       /* a                                                               */
+    double viscosity;    /* mu                                                              */
+    int32_t j1_rule;     /* 0: j_1 = first source; 1: splitmix64 hash of (seed, block)      */
+    uint64_t seed;       /* seed of the j_1 hash                                            */
+    int32_t shard_id;    /* this shard's share of the block work lists                      */
+    int32_t n_shards;    /* number of shards (1 = everything)                               */
+    int32_t flags;       /* reserved, 0                                                     */
+} hh_params;
+
+/* Fills *p with the defaults: leaf 32, eta 1, eps 1e-4, max_rank 48, FP32,
+ * MLP, a = mu = 1, j1_rule 0, seed 0, one shard, no flags. */
+void hh_default_params(hh_params *p);
+
+/* Context: owns the MLP weights copy, a device status word and counters.
+ * device: CUDA ordinal.  Leaves the caller's current device unchanged. */
+hh_status hh_create(hh_ctx **ctx, int device);
+void hh_destroy(hh_ctx *ctx);
+/* Message of the last failing call on ctx (never NULL; "" if none). */
+const char *hh_last_error(const hh_ctx *ctx);
+
+/* Loads the pair MLP h-hat of Eq. 4: theta_dev is a device float32 vector of
+ * the packed parameters of 4 -> width -> width -> width -> 6 (depth must be
+ * 3, width 32 or 64).  The library copies it; the caller keeps ownership. */
+hh_status hh_set_mlp(hh_ctx *ctx, const float *theta_dev, int width, int depth, void *stream);
+
+/* Cluster tree (Definition 1, Section 3.1).  X_dev: [N, 3] FP64 device.
+ * offsets: host array of batch+1 particle offsets (instance b owns rows
+ * offsets[b] .. offsets[b+1]-1); batch = 1 with offsets = {0, N} for a
+ * single suspension.  Per instance: Morton codes on a 2^21 grid of the
+ * instance's bounding cube, a stable radix sort, breadth-first bisection at
+ * the highest differing code bit, bounding boxes.  Synchronises the stream
+ * once per tree level.  N < 2^30. */
+hh_status hh_build_tree(hh_ctx *ctx, const double *X_dev, const int64_t *offsets, int32_t batch,
+                        const hh_params *p, void *stream, hh_tree **out);
+
+/* Admissibility partition (Eq. 7, Algorithm 1) of every instance of the tree
+ * into admissible blocks P^G and inadmissible leaf blocks P^H, each sorted by
+ * (target, source) node id.  Blocks whose boxes touch (dist = 0) are never
+ * admissible.  Synchronises once per frontier level. */
+hh_status hh_partition(hh_ctx *ctx, const hh_tree *tree, const hh_params *p, void *stream, hh_blocks **out);
+
+/* Block ACA (Algorithm 2) on every admissible block; stores the factors C, Q
+ * and the pivots resident in device memory (sum_b (|tau_b| + |sigma_b|) *
+ * rank_b * 9 reals).  Runs the rank loop twice (sizes, then factors) and
+ * synchronises between.  Returns HH_WARN_RANK_CAP if a block stopped at
+ * max_rank before meeting Eq. 10. */
+hh_status hh_aca(hh_ctx *ctx, const hh_tree *tree, const hh_blocks *blocks, const hh_params *p, void *stream,
+                 hh_hmat **out);
+
+/* U_dev = alpha_1 F + M_H F (transpose = 0) or alpha_1 F + M_H^T F
+ * (transpose = 1), FP64 [N, 3] in the caller's particle order.  Inadmissible
+ * blocks are recomputed from the pair kernel on every call; admissible
+ * blocks use the stored factors.  Synchronises once (work-list sizes). */
+hh_status hh_matvec(hh_ctx *ctx, const hh_hmat *h, const double *F_dev, double *U_dev, int transpose,
+                    void *stream);
+
+/* One prediction U = M(X) F end to end (tree, partition, ACA fused with the
+ * low-rank apply, inadmissible blocks, FP64 accumulation) without keeping
+ * the factors: each admissible block's C and Q live only in a bounded
+ * per-team workspace.  This is the per-time-step call of Section 2.4.
+ * X_dev, F_dev, U_dev: [N, 3] FP64 device, N = offsets[batch].  Synchronises
+ * as hh_build_tree and hh_partition do. */
+hh_status hh_predict(hh_ctx *ctx, const double *X_dev, const double *F_dev, const int64_t *offsets,
+                     int32_t batch, const hh_params *p, void *stream, double *U_dev);
+
+/* Adjoint of L = sum_i gU_i . U_i for U = alpha_1 F + M_H F built by hh_aca
+ * with the MLP kernel: gF_dev = alpha_1 gU + M_H^T gU (FP64 [N,3]),
+ * gX_dev += dL/dX (FP64 [N,3]) and gtheta_dev += dL/dtheta (float32, length
+ * of theta), the last two with tree, partition and pivots frozen.  Any of
+ * gF_dev, gX_dev, gtheta_dev may be NULL; gX and gtheta are accumulated
+ * into (zero them first).  Near-field activations are recomputed, not
+ * stored. */
+hh_status hh_matvec_backward(hh_ctx *ctx, const hh_hmat *h, const double *gU_dev, const double *F_dev,
+                             double *gF_dev, double *gX_dev, float *gtheta_dev, void *stream);
+
+/* Copies the tree to host buffers (any pointer may be NULL).  perm[N]: input
+ * row of each sorted position; codes[N]: sorted Morton codes; node arrays of
+ * length n_nodes (child is [n_nodes, 2], -1 for leaves; lo/hi [n_nodes, 3]).
+ * Synchronises the device. */
+hh_status hh_export_tree(const hh_tree *tree, int32_t *perm, uint64_t *codes, int32_t *node_begin,
+                         int32_t *node_end, int32_t *node_child, double *node_lo, double *node_hi,
+                         int64_t *n_nodes, int64_t *n);
+
+/* Copies the block lists ([n, 2] (target, source) node ids, sorted) to host
+ * buffers (NULL pointers skipped).  Synchronises the device. */
+hh_status hh_export_blocks(const hh_blocks *blocks, int32_t *PG, int64_t *nG, int32_t *PH, int64_t *nH);
+
+/* Copies the per-block ACA ranks ([nG]) and pivots ([nG, max_rank]
+ * block-local row / column indices, -1 past the rank) to host buffers. */
+hh_status hh_export_aca(const hh_hmat *h, int32_t *ranks, int32_t *piv_rows, int32_t *piv_cols, int64_t *nG,
+                        int32_t *max_rank);
+
+typedef struct {
+    double t_tree, t_part, t_near, t_aca, t_apply, t_acc; /* ms of the last call's stages (CUDA events) */
+    int64_t n_near_pairs;   /* pair-kernel evaluations in inadmissible blocks */
+    int64_t n_aca_queries;  /* pair-kernel evaluations inside ACA            */
+    int64_t n_blocks_G, n_blocks_H, n_nodes;
+    int64_t rank_hist[65];  /* rank_hist[min(rank, 64)] (hh_aca only)        */
+} hh_stats_t;
+
+/* Counters of the last hh_predict / hh_aca on ctx. */
+hh_status hh_stats(hh_ctx *ctx, hh_stats_t *out);
+
+void hh_tree_free(hh_tree *t);
+void hh_blocks_free(hh_blocks *b);
+void hh_hmat_free(hh_hmat *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HHIGNN_H */

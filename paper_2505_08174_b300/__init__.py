@@ -1,0 +1,286 @@
+"""B300-native H-HIGNN mobility product: thin Python binding of libhhignn.so.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library (``csrc/``), reached through the C-ABI of ``include/hhignn.h``.
+PyTorch supplies device memory and streams.  There is no CPU fallback: if the
+shared library is missing or cannot be loaded, ``lib()`` raises.
+
+    import torch, paper_2505_08174_b300 as hh
+    ctx = hh.Context()
+    ctx.set_mlp(theta, width=32)
+    U = ctx.predict(X, F, hh.Params(eps=1e-4))          # X, F: [N,3] float64 cuda
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhhignn.so")
+
+HH_OK, HH_ERR_ARG, HH_ERR_CUDA, HH_ERR_OOM, HH_ERR_TIMEOUT, HH_ERR_NUMERIC, HH_WARN_RANK_CAP = range(7)
+HH_FP64, HH_FP32, HH_BF16 = 0, 1, 2
+HH_MLP, HH_RPY = 0, 1
+STATUS_NAMES = {0: "HH_OK", 1: "HH_ERR_ARG", 2: "HH_ERR_CUDA", 3: "HH_ERR_OOM", 4: "HH_ERR_TIMEOUT",
+                5: "HH_ERR_NUMERIC", 6: "HH_WARN_RANK_CAP"}
+PRECISIONS = {"fp64": HH_FP64, "fp32": HH_FP32, "bf16": HH_BF16}
+KERNELS = {"mlp": HH_MLP, "rpy": HH_RPY}
+
+# Every function the header declares (checked by the CPU test-suite).
+EXPORTS = [
+    "hh_default_params", "hh_create", "hh_destroy", "hh_last_error", "hh_set_mlp", "hh_build_tree",
+    "hh_partition", "hh_aca", "hh_matvec", "hh_predict", "hh_matvec_backward", "hh_export_tree",
+    "hh_export_blocks", "hh_export_aca", "hh_stats", "hh_tree_free", "hh_blocks_free", "hh_hmat_free",
+]
+
+
+class HHError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class CParams(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int32), ("eta", ctypes.c_double), ("eps", ctypes.c_double),
+                ("max_rank", ctypes.c_int32), ("precision", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("radius", ctypes.c_double), ("viscosity", ctypes.c_double), ("j1_rule", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("shard_id", ctypes.c_int32), ("n_shards", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+class CStats(ctypes.Structure):
+    _fields_ = [("t_tree", ctypes.c_double), ("t_part", ctypes.c_double), ("t_near", ctypes.c_double),
+                ("t_aca", ctypes.c_double), ("t_apply", ctypes.c_double), ("t_acc", ctypes.c_double),
+                ("n_near_pairs", ctypes.c_int64), ("n_aca_queries", ctypes.c_int64),
+                ("n_blocks_G", ctypes.c_int64), ("n_blocks_H", ctypes.c_int64), ("n_nodes", ctypes.c_int64),
+                ("rank_hist", ctypes.c_int64 * 65)]
+
+
+_P = ctypes.c_void_p
+_lib = None
+
+
+def lib():
+    """Load libhhignn.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} not built; run `python -m paper_2505_08174_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        i32, i64, st = ctypes.c_int32, ctypes.c_int64, ctypes.c_int
+        sig = {
+            "hh_default_params": (None, [_P]),
+            "hh_create": (st, [_P, ctypes.c_int]),
+            "hh_destroy": (None, [_P]),
+            "hh_last_error": (ctypes.c_char_p, [_P]),
+            "hh_set_mlp": (st, [_P, _P, ctypes.c_int, ctypes.c_int, _P]),
+            "hh_build_tree": (st, [_P, _P, _P, i32, _P, _P, _P]),
+            "hh_partition": (st, [_P, _P, _P, _P, _P]),
+            "hh_aca": (st, [_P, _P, _P, _P, _P, _P]),
+            "hh_matvec": (st, [_P, _P, _P, _P, ctypes.c_int, _P]),
+            "hh_predict": (st, [_P, _P, _P, _P, i32, _P, _P, _P]),
+            "hh_matvec_backward": (st, [_P, _P, _P, _P, _P, _P, _P, _P]),
+            "hh_export_tree": (st, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+            "hh_export_blocks": (st, [_P, _P, _P, _P, _P]),
+            "hh_export_aca": (st, [_P, _P, _P, _P, _P, _P]),
+            "hh_stats": (st, [_P, _P]),
+            "hh_tree_free": (None, [_P]),
+            "hh_blocks_free": (None, [_P]),
+            "hh_hmat_free": (None, [_P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def Params(leaf_size=32, eta=1.0, eps=1e-4, max_rank=48, precision="fp32", kernel="mlp", radius=1.0,
+           viscosity=1.0, j1_rule=0, seed=0, shard_id=0, n_shards=1) -> CParams:
+    p = CParams()
+    lib().hh_default_params(ctypes.byref(p))
+    p.leaf_size, p.eta, p.eps, p.max_rank = leaf_size, eta, eps, max_rank
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
+    p.kernel = KERNELS[kernel] if isinstance(kernel, str) else kernel
+    p.radius, p.viscosity, p.j1_rule, p.seed = radius, viscosity, j1_rule, seed
+    p.shard_id, p.n_shards = shard_id, n_shards
+    return p
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_xyz(t, name):
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.dim() == 2 and t.shape[1] == 3 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous [N,3] float64 CUDA tensor")
+
+
+class Context:
+    """One hh_ctx on a CUDA device (owns the MLP copy, counters, status)."""
+
+    def __init__(self, device: int | None = None):
+        import torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self._h = ctypes.c_void_p()
+        self._check(lib().hh_create(ctypes.byref(self._h), self.device), "hh_create")
+        self.width = None
+
+    def _check(self, st, what, allow_warn=True):
+        if st == HH_OK or (allow_warn and st == HH_WARN_RANK_CAP):
+            return st
+        msg = lib().hh_last_error(self._h).decode() if getattr(self, "_h", None) else ""
+        raise HHError(st, f"{what}: {msg}")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_mlp(self, theta, width: int, stream=None):
+        import torch
+        th = torch.as_tensor(theta, dtype=torch.float32).to(f"cuda:{self.device}").contiguous()
+        self._check(lib().hh_set_mlp(self._h, _dptr(th), width, 3, _stream(stream)), "hh_set_mlp")
+        torch.cuda.current_stream().synchronize()
+        self.width = width
+
+    def predict(self, X, F, params: CParams, offsets=None, out=None, stream=None):
+        """U = alpha_1 F + M_H F end to end (tree, partition, fused ACA, near, FP64 sum)."""
+        import torch
+        _check_xyz(X, "X"); _check_xyz(F, "F")
+        n = X.shape[0]
+        off = np.asarray([0, n] if offsets is None else offsets, dtype=np.int64)
+        U = torch.empty_like(X) if out is None else out
+        st = lib().hh_predict(self._h, _dptr(X), _dptr(F), off.ctypes.data_as(_P), len(off) - 1,
+                              ctypes.byref(params), _stream(stream), _dptr(U))
+        self.last_status = self._check(st, "hh_predict")
+        return U
+
+    def stats(self) -> dict:
+        s = CStats()
+        self._check(lib().hh_stats(self._h, ctypes.byref(s)), "hh_stats")
+        d = {f: getattr(s, f) for f, _ in CStats._fields_ if f != "rank_hist"}
+        d["rank_hist"] = list(s.rank_hist)
+        return d
+
+    # -- staged API -----------------------------------------------------------
+    def build_tree(self, X, params: CParams, offsets=None, stream=None):
+        _check_xyz(X, "X")
+        off = np.asarray([0, X.shape[0]] if offsets is None else offsets, dtype=np.int64)
+        h = ctypes.c_void_p()
+        self._check(lib().hh_build_tree(self._h, _dptr(X), off.ctypes.data_as(_P), len(off) - 1,
+                                        ctypes.byref(params), _stream(stream), ctypes.byref(h)), "hh_build_tree")
+        return Tree(self, h)
+
+    def partition(self, tree, params: CParams, stream=None):
+        h = ctypes.c_void_p()
+        self._check(lib().hh_partition(self._h, tree._h, ctypes.byref(params), _stream(stream), ctypes.byref(h)),
+                    "hh_partition")
+        return Blocks(self, h, tree)
+
+    def aca(self, tree, blocks, params: CParams, stream=None):
+        h = ctypes.c_void_p()
+        st = lib().hh_aca(self._h, tree._h, blocks._h, ctypes.byref(params), _stream(stream), ctypes.byref(h))
+        self._check(st, "hh_aca")
+        hm = HMatrix(self, h, tree, blocks, params)
+        hm.status = st
+        return hm
+
+    def matvec(self, hmat, F, transpose=False, out=None, stream=None):
+        import torch
+        _check_xyz(F, "F")
+        U = torch.empty_like(F) if out is None else out
+        self._check(lib().hh_matvec(self._h, hmat._h, _dptr(F), _dptr(U), int(transpose), _stream(stream)),
+                    "hh_matvec")
+        return U
+
+    def matvec_backward(self, hmat, gU, F, gF=None, gX=None, gtheta=None, stream=None):
+        p = lambda t: _dptr(t) if t is not None else None
+        self._check(lib().hh_matvec_backward(self._h, hmat._h, _dptr(gU), _dptr(F), p(gF), p(gX), p(gtheta),
+                                             _stream(stream)), "hh_matvec_backward")
+
+
+class _Owned:
+    _free = None
+
+    def __init__(self, ctx, h):
+        self.ctx, self._h = ctx, h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            getattr(lib(), self._free)(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Tree(_Owned):
+    _free = "hh_tree_free"
+
+    def export(self):
+        nn, n = ctypes.c_int64(), ctypes.c_int64()
+        self.ctx._check(lib().hh_export_tree(self._h, None, None, None, None, None, None, None,
+                                             ctypes.byref(nn), ctypes.byref(n)), "hh_export_tree")
+        nn, n = nn.value, n.value
+        perm = np.zeros(n, np.int32); codes = np.zeros(n, np.uint64)
+        nb = np.zeros(nn, np.int32); ne = np.zeros(nn, np.int32); ch = np.zeros((nn, 2), np.int32)
+        lo = np.zeros((nn, 3)); hi = np.zeros((nn, 3))
+        q = lambda a: a.ctypes.data_as(_P)
+        self.ctx._check(lib().hh_export_tree(self._h, q(perm), q(codes), q(nb), q(ne), q(ch), q(lo), q(hi),
+                                             None, None), "hh_export_tree")
+        return dict(perm=perm, codes=codes, begin=nb, end=ne, child=ch, lo=lo, hi=hi)
+
+
+class Blocks(_Owned):
+    _free = "hh_blocks_free"
+
+    def __init__(self, ctx, h, tree):
+        super().__init__(ctx, h)
+        self.tree = tree    # keep the tree alive
+
+    def export(self):
+        nG, nH = ctypes.c_int64(), ctypes.c_int64()
+        self.ctx._check(lib().hh_export_blocks(self._h, None, ctypes.byref(nG), None, ctypes.byref(nH)),
+                        "hh_export_blocks")
+        G = np.zeros((nG.value, 2), np.int32); H = np.zeros((nH.value, 2), np.int32)
+        self.ctx._check(lib().hh_export_blocks(self._h, G.ctypes.data_as(_P), None, H.ctypes.data_as(_P), None),
+                        "hh_export_blocks")
+        return G, H
+
+
+class HMatrix(_Owned):
+    _free = "hh_hmat_free"
+
+    def __init__(self, ctx, h, tree, blocks, params):
+        super().__init__(ctx, h)
+        self.tree, self.blocks, self.params = tree, blocks, params
+
+    def export(self):
+        nG, mr = ctypes.c_int64(), ctypes.c_int32()
+        self.ctx._check(lib().hh_export_aca(self._h, None, None, None, ctypes.byref(nG), ctypes.byref(mr)),
+                        "hh_export_aca")
+        ranks = np.zeros(nG.value, np.int32)
+        pI = np.zeros((nG.value, mr.value), np.int32); pJ = np.zeros((nG.value, mr.value), np.int32)
+        self.ctx._check(lib().hh_export_aca(self._h, ranks.ctypes.data_as(_P), pI.ctypes.data_as(_P),
+                                            pJ.ctypes.data_as(_P), None, None), "hh_export_aca")
+        return ranks, pI, pJ

@@ -1,0 +1,741 @@
+// hh_aca.cu -- batched block adaptive cross approximation (Algorithm 2,
+// Eqs. 8-10) and the low-rank product C (Q F) (Eq. 8) on the GPU.
+//
+// Design: persistent "team" kernels.  A team is one warp (blocks whose
+// clusters have <= 128 particles) or one 256-thread CTA (larger blocks).  A
+// team pulls the next admissible block from a work list (atomic counter,
+// largest blocks first), runs the whole rank loop of Algorithm 2 on it, and
+// -- in the fused mode used by hh_predict -- applies the block to F right
+// away, so C and Q only ever live in the team's private workspace (bounded,
+// independent of N).  Results are written per block, so the output does not
+// depend on which team ran which block.
+//
+// Per rank step k (element = 3x3 block, row-major):
+//   column  c_k(m) = G(m, j_k) - sum_{p<k} C_p(m) Q_p(j_k)
+//   i_k     = argmax over unused rows of |c_k(m)|_F, ties -> lowest index
+//   c_k    <- c_k [c_k(i_k)]^-1, inverse in FP64 (adjugate)
+//   row     q_k(n) = G(i_k, n) - sum_{p<k} C_p(i_k) Q_p(n)
+//   j_{k+1} = argmax over unused columns of |q_k(n)|_F
+//   A_pk = sum_m c_p(m)^T c_k(m),  B_kp = sum_n q_k(n) q_p(n)^T (3x3 Grams)
+//   nu^2 = tr(A_kk B_kk), lambda^2 += nu^2 + 2 sum_{p<k} tr(A_pk B_kp)
+//   stop if nu^2 <= zeta^2 lambda^2, or k = min(c, q), or k = max_rank
+// Pivot guard: a pivot element with det = 0 or 1/(|P|_F |P^-1|_F) < 1e-10
+// is replaced by the unused row of largest |det|; a zero column residual (or
+// no usable pivot) ends the block with the pairs found so far.
+// Gram partial sums are formed in the working precision and reduced, and
+// the norm recurrence is kept, in FP64.
+#include <algorithm>
+
+#include "hh_internal.h"
+
+namespace {
+
+constexpr int MAXR = 64;          // hard cap on max_rank
+constexpr int WARP_ROWS = 4;      // warp team: up to 128 rows / columns per block
+constexpr int CTA_T = 256;        // CTA team size
+constexpr int SMALL_MAX = 32 * WARP_ROWS;
+
+template <typename R>
+struct AcaArgs {
+    const double* Xs;
+    const R* th_g;   // parameters in global memory (copied to shared)
+    int n_th;
+    PairParams pp;
+    const double* Fs;
+    const int32_t* PG;
+    const int32_t* nbeg;
+    const int32_t* nend;
+    const int32_t* work;
+    int64_t n_work;
+    unsigned long long* counter;
+    int max_rank;
+    double eps2;
+    int j1_rule;
+    uint64_t seed;
+    R* scratch;
+    int64_t team_stride;   // reals per team
+    int32_t* rank;
+    int32_t* pivI;
+    int32_t* pivJ;
+    R* part;
+    const int64_t* pofs;
+    R* fac;
+    const int64_t* fofs;
+    unsigned* status;
+    unsigned long long* n_queries;
+};
+
+template <typename R>
+struct alignas(16) TeamSmem {
+    R qj[MAXR * 9];        // Q_p(j_k), p < k
+    R ci[MAXR * 9];        // C_p(i_k), p < k
+    double A[(MAXR + 1) * 9];
+    double tr[MAXR + 1];
+    R Pi[9];
+    R tv[MAXR * 3];
+    double rv[8];
+    int ri[8];
+    int flag, stop;
+};
+
+__device__ __forceinline__ uint64_t splitmix_once(uint64_t x)
+{
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// j_1 (drawn at random in the paper): rule 0 = first source, rule 1 =
+// splitmix64(seed ^ (t << 32) ^ s) mod q.
+__device__ __forceinline__ int j1_of(int rule, uint64_t seed, int t, int s, int q)
+{
+    if (rule == 0 || q <= 1) return 0;
+    uint64_t h = splitmix_once(seed ^ ((uint64_t)(uint32_t)t << 32) ^ (uint64_t)(uint32_t)s);
+    return (int)(h % (uint64_t)q);
+}
+
+// ---- teams -----------------------------------------------------------------
+struct WarpTeam {
+    static constexpr int SIZE = 32;
+    static constexpr int ROWS = WARP_ROWS;   // rows per thread
+    static constexpr int NW = 1;
+    static constexpr bool REG_FLAGS = true;  // used-row/column flags in registers
+    __device__ __forceinline__ int tid() const { return threadIdx.x & 31; }
+    __device__ __forceinline__ int warp() const { return 0; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    template <typename T, typename S>
+    __device__ __forceinline__ void argmax(T& v, int& i, S&) const { warp_argmax(v, i); }
+};
+
+struct CtaTeam {
+    static constexpr int SIZE = CTA_T;
+    static constexpr int ROWS = 1 << 20;      // unbounded (loops exit at c / q)
+    static constexpr int NW = CTA_T / 32;
+    static constexpr bool REG_FLAGS = false;  // flags as bytes in the team workspace
+    __device__ __forceinline__ int tid() const { return threadIdx.x; }
+    __device__ __forceinline__ int warp() const { return threadIdx.x >> 5; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    template <typename T, typename S>
+    __device__ __forceinline__ void argmax(T& v, int& i, S& sm) const
+    {
+        warp_argmax(v, i);
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        __syncthreads();
+        if (lane == 0) { sm.rv[w] = (double)v; sm.ri[w] = i; }
+        __syncthreads();
+        double bv = sm.rv[0];
+        int bi = sm.ri[0];
+        for (int k = 1; k < NW; ++k) {
+            double ov = sm.rv[k];
+            int oi = sm.ri[k];
+            if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+        }
+        v = (T)bv;
+        i = bi;
+        __syncthreads();
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ void ld9(const R* __restrict__ base, int64_t stride, int64_t idx, R* v)
+{
+#pragma unroll
+    for (int e = 0; e < 9; ++e) v[e] = base[e * stride + idx];
+}
+template <typename R>
+__device__ __forceinline__ void st9(R* __restrict__ base, int64_t stride, int64_t idx, const R* v)
+{
+#pragma unroll
+    for (int e = 0; e < 9; ++e) base[e * stride + idx] = v[e];
+}
+
+// sm.A[p] = sum_x C_p(x)^T C_k(x) for p = 0..k (each warp of the team owns a
+// subset of p and sweeps all rows with its 32 lanes).
+template <typename R, class Team>
+__device__ void gram_cols(const Team& tm, TeamSmem<R>& sm, const R* Cs, int c, int k)
+{
+    const int lane = threadIdx.x & 31;
+    const R* Ck = Cs + (int64_t)k * 9 * c;
+    for (int p = tm.warp(); p <= k; p += Team::NW) {
+        const R* Cp = Cs + (int64_t)p * 9 * c;
+        R acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int x = lane; x < c; x += 32) {
+            R a[9], b[9];
+            ld9(Cp, c, x, a);
+            ld9(Ck, c, x, b);
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+#pragma unroll
+                for (int v = 0; v < 3; ++v) acc[3 * u + v] += a[u] * b[v] + a[3 + u] * b[3 + v] + a[6 + u] * b[6 + v];
+        }
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            double s = warp_sum((double)acc[e]);
+            if (lane == 0) sm.A[9 * p + e] = s;
+        }
+    }
+}
+
+// sm.tr[p] = tr(A_pk B_kp) with B_kp = sum_n q_k(n) q_p(n)^T, p = 0..k.
+template <typename R, class Team>
+__device__ void gram_rows(const Team& tm, TeamSmem<R>& sm, const R* Qs, int q, int k)
+{
+    const int lane = threadIdx.x & 31;
+    const R* Qk = Qs + (int64_t)k * 9 * q;
+    for (int p = tm.warp(); p <= k; p += Team::NW) {
+        const R* Qp = Qs + (int64_t)p * 9 * q;
+        R acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int x = lane; x < q; x += 32) {
+            R a[9], b[9];
+            ld9(Qk, q, x, a);
+            ld9(Qp, q, x, b);
+#pragma unroll
+            for (int u = 0; u < 3; ++u)
+#pragma unroll
+                for (int v = 0; v < 3; ++v)
+                    acc[3 * u + v] += a[3 * u] * b[3 * v] + a[3 * u + 1] * b[3 * v + 1] + a[3 * u + 2] * b[3 * v + 2];
+        }
+        double trv = 0.0;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            double s = warp_sum((double)acc[e]);  // B_kp[u][v], e = 3u + v
+            const int u = e / 3, v = e % 3;
+            trv += sm.A[9 * p + 3 * v + u] * s;    // tr(A B) = sum_{u,v} A[v][u] B[u][v]
+        }
+        if (lane == 0) sm.tr[p] = trv;
+    }
+}
+
+// ---- the per-block ACA -----------------------------------------------------
+template <typename R, int KIND, class Team>
+__device__ void aca_block(const AcaArgs<R>& A, const Team& tm, TeamSmem<R>& sm, const R* th, R* Cs_base, int64_t b,
+                          int mode)
+{
+    constexpr int ROWS = Team::ROWS, SIZE = Team::SIZE;
+    constexpr int NB = Team::REG_FLAGS ? (ROWS + 31) / 32 : 1;
+    const int tid = tm.tid();
+    const int32_t t = A.PG[2 * b], s = A.PG[2 * b + 1];
+    const int32_t t0 = A.nbeg[t], c = A.nend[t] - t0, s0 = A.nbeg[s], q = A.nend[s] - s0;
+    const int kmax = min(min(c, q), A.max_rank);
+    R* Cs = Cs_base;
+    R* Qs = Cs_base + (int64_t)kmax * 9 * c;
+    // used-row / used-column flags: register bitmasks (warp team, bit i of the
+    // thread's i-th row) or bytes after the factors (CTA team)
+    uint32_t usedR[NB], usedC[NB];
+    uint8_t* fR = reinterpret_cast<uint8_t*>(Qs + (int64_t)kmax * 9 * q);
+    uint8_t* fC = fR + c;
+#pragma unroll
+    for (int i = 0; i < NB; ++i) usedR[i] = usedC[i] = 0u;
+    if constexpr (!Team::REG_FLAGS) {
+        for (int x = tid; x < c + q; x += SIZE) fR[x] = 0;
+        tm.sync();
+    }
+    auto is_used = [&](const uint32_t* u, const uint8_t* f, int i, int x) -> bool {
+        if constexpr (Team::REG_FLAGS) return (u[i >> 5] >> (i & 31)) & 1u;
+        else return f[x] != 0;
+    };
+    auto set_used = [&](uint32_t* u, uint8_t* f, int x) {
+        if constexpr (Team::REG_FLAGS) {
+            if (x % SIZE == tid) u[(x / SIZE) >> 5] |= 1u << ((x / SIZE) & 31);
+        } else {
+            if (tid == 0) f[x] = 1;
+        }
+    };
+    int j = j1_of(A.j1_rule, A.seed, t, s, q);
+    set_used(usedC, fC, j);
+    double lam2 = 0.0;
+    int k = 0;
+    bool capped = false;
+    while (k < kmax) {
+        // Q_p(j_k), p < k
+        for (int idx = tid; idx < k * 9; idx += SIZE) sm.qj[idx] = Qs[(int64_t)idx * q + j];
+        tm.sync();
+        // column residual (unscaled) and row-pivot candidates
+        R best = (R)-1;
+        int bi = -1;
+#pragma unroll 1
+        for (int i = 0; i < ROWS; ++i) {
+            const int m = tid + SIZE * i;
+            if (m >= c) break;
+            R rx, ry, rz, K[9];
+            sep<R>(A.Xs, t0 + m, s0 + j, rx, ry, rz);
+            pair_block<R, KIND>(th, A.pp, rx, ry, rz, K);
+            for (int p = 0; p < k; ++p) {
+                R cp[9], t9[9];
+                ld9(Cs + (int64_t)p * 9 * c, c, m, cp);
+                mm3(cp, sm.qj + 9 * p, t9);
+#pragma unroll
+                for (int e = 0; e < 9; ++e) K[e] -= t9[e];
+            }
+            st9(Cs + (int64_t)k * 9 * c, c, m, K);
+            if (!is_used(usedR, fR, i, m)) {
+                R v = fro2(K);
+                if (v > best) { best = v; bi = m; }
+            }
+        }
+        tm.argmax(best, bi, sm);
+        if (bi < 0 || !(best > (R)0)) break;
+        tm.sync();
+        if (tid == 0) {
+            double P[9], Pi[9];
+#pragma unroll
+            for (int e = 0; e < 9; ++e) P[e] = (double)Cs[((int64_t)k * 9 + e) * c + bi];
+            double det = inv3d(P, Pi);
+            double rc = det != 0.0 ? 1.0 / sqrt(fro2(P) * fro2(Pi)) : 0.0;
+            int bad = !(det != 0.0) || !(rc >= 1e-10);
+            sm.flag = bad;
+            if (!bad)
+#pragma unroll
+                for (int e = 0; e < 9; ++e) sm.Pi[e] = (R)Pi[e];
+        }
+        tm.sync();
+        if (sm.flag) {
+            double bd = 0.0;
+            int bj = -1;
+            for (int i = 0; i < ROWS; ++i) {
+                const int m = tid + SIZE * i;
+                if (m >= c) break;
+                if (is_used(usedR, fR, i, m)) continue;
+                double P[9];
+#pragma unroll
+                for (int e = 0; e < 9; ++e) P[e] = (double)Cs[((int64_t)k * 9 + e) * c + m];
+                double dv = fabs(det3d(P));
+                if (dv > bd) { bd = dv; bj = m; }
+            }
+            tm.argmax(bd, bj, sm);
+            if (bj < 0) break;
+            bi = bj;
+            if (tid == 0) {
+                double P[9], Pi[9];
+#pragma unroll
+                for (int e = 0; e < 9; ++e) P[e] = (double)Cs[((int64_t)k * 9 + e) * c + bi];
+                inv3d(P, Pi);
+#pragma unroll
+                for (int e = 0; e < 9; ++e) sm.Pi[e] = (R)Pi[e];
+            }
+            tm.sync();
+        }
+        set_used(usedR, fR, bi);
+        if (tid == 0 && A.pivI) {
+            A.pivI[b * A.max_rank + k] = bi;
+            A.pivJ[b * A.max_rank + k] = j;
+        }
+        // c_k <- c_k [c_k(i_k)]^-1
+        R Pi[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) Pi[e] = sm.Pi[e];
+        for (int i = 0; i < ROWS; ++i) {
+            const int m = tid + SIZE * i;
+            if (m >= c) break;
+            R r[9], o[9];
+            ld9(Cs + (int64_t)k * 9 * c, c, m, r);
+            mm3(r, Pi, o);
+            st9(Cs + (int64_t)k * 9 * c, c, m, o);
+        }
+        tm.sync();
+        gram_cols<R>(tm, sm, Cs, c, k);
+        for (int idx = tid; idx < k * 9; idx += SIZE) sm.ci[idx] = Cs[(int64_t)idx * c + bi];
+        tm.sync();
+        // row residual and column-pivot candidates
+        R bestc = (R)-1;
+        int bj = -1;
+        for (int i = 0; i < ROWS; ++i) {
+            const int n = tid + SIZE * i;
+            if (n >= q) break;
+            R rx, ry, rz, K[9];
+            sep<R>(A.Xs, t0 + bi, s0 + n, rx, ry, rz);
+            pair_block<R, KIND>(th, A.pp, rx, ry, rz, K);
+            for (int p = 0; p < k; ++p) {
+                R qp[9], t9[9];
+                ld9(Qs + (int64_t)p * 9 * q, q, n, qp);
+                mm3(sm.ci + 9 * p, qp, t9);
+#pragma unroll
+                for (int e = 0; e < 9; ++e) K[e] -= t9[e];
+            }
+            st9(Qs + (int64_t)k * 9 * q, q, n, K);
+            if (!is_used(usedC, fC, i, n)) {
+                R v = fro2(K);
+                if (v > bestc) { bestc = v; bj = n; }
+            }
+        }
+        tm.argmax(bestc, bj, sm);
+        tm.sync();
+        gram_rows<R>(tm, sm, Qs, q, k);
+        tm.sync();
+        if (tid == 0) {
+            double nu2 = sm.tr[k], cross = 0.0;
+            for (int p = 0; p < k; ++p) cross += sm.tr[p];
+            lam2 = lam2 + nu2 + 2.0 * cross;
+            sm.stop = (nu2 <= A.eps2 * lam2) || (bj < 0);
+        }
+        tm.sync();
+        ++k;
+        const bool stop = sm.stop;
+        tm.sync();
+        if (stop) break;
+        if (k == kmax) {
+            capped = (k == A.max_rank) && (k < min(c, q));
+            break;
+        }
+        j = bj;
+        set_used(usedC, fC, j);
+    }
+    const int l = k;
+    if (tid == 0) {
+        if (A.rank) A.rank[b] = l;
+        if (A.pivI)
+            for (int p = l; p < A.max_rank; ++p) { A.pivI[b * A.max_rank + p] = -1; A.pivJ[b * A.max_rank + p] = -1; }
+        if (capped) atomicOr(A.status, (unsigned)HH_DEV_RANK_CAP);
+        atomicAdd(A.n_queries, (unsigned long long)(c + q) * (unsigned long long)l);
+    }
+    if (mode == 0) {
+        // fused apply: t_p = sum_n Q_p(n) F(s0+n); y(m) = sum_p C_p(m) t_p
+        const int lane = threadIdx.x & 31;
+        for (int p = tm.warp(); p < l; p += Team::NW) {
+            const R* Qp = Qs + (int64_t)p * 9 * q;
+            R a0 = 0, a1 = 0, a2 = 0;
+            for (int n = lane; n < q; n += 32) {
+                R qv[9];
+                ld9(Qp, q, n, qv);
+                const double* f = A.Fs + 3 * (int64_t)(s0 + n);
+                R f0 = (R)f[0], f1 = (R)f[1], f2 = (R)f[2];
+                a0 += qv[0] * f0 + qv[1] * f1 + qv[2] * f2;
+                a1 += qv[3] * f0 + qv[4] * f1 + qv[5] * f2;
+                a2 += qv[6] * f0 + qv[7] * f1 + qv[8] * f2;
+            }
+            a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2);
+            if (lane == 0) { sm.tv[3 * p] = a0; sm.tv[3 * p + 1] = a1; sm.tv[3 * p + 2] = a2; }
+        }
+        tm.sync();
+        R* out = A.part + 3 * A.pofs[b];
+        for (int i = 0; i < ROWS; ++i) {
+            const int m = tid + SIZE * i;
+            if (m >= c) break;
+            R y0 = 0, y1 = 0, y2 = 0;
+            for (int p = 0; p < l; ++p) {
+                R cv[9];
+                ld9(Cs + (int64_t)p * 9 * c, c, m, cv);
+                const R* tp = sm.tv + 3 * p;
+                y0 += cv[0] * tp[0] + cv[1] * tp[1] + cv[2] * tp[2];
+                y1 += cv[3] * tp[0] + cv[4] * tp[1] + cv[5] * tp[2];
+                y2 += cv[6] * tp[0] + cv[7] * tp[1] + cv[8] * tp[2];
+            }
+            out[3 * m] = y0; out[3 * m + 1] = y1; out[3 * m + 2] = y2;
+        }
+    } else if (mode == 2) {
+        R* dst = A.fac + 9 * A.fofs[b];
+        const int64_t nc = (int64_t)l * 9 * c, nq = (int64_t)l * 9 * q;
+        for (int64_t x = tid; x < nc; x += SIZE) dst[x] = Cs[x];
+        for (int64_t x = tid; x < nq; x += SIZE) dst[nc + x] = Qs[x];
+    }
+    tm.sync();
+}
+
+template <typename R>
+__device__ void load_theta(const AcaArgs<R>& A, R* th)
+{
+    for (int i = threadIdx.x; i < A.n_th; i += blockDim.x) th[i] = A.th_g[i];
+    __syncthreads();
+}
+
+constexpr int WPB = 4;  // warp teams per CTA
+
+template <typename R, int KIND>
+__global__ void __launch_bounds__(32 * WPB) k_aca_warp(AcaArgs<R> A, int mode)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TeamSmem<R>* sms = reinterpret_cast<TeamSmem<R>*>(smem_raw);
+    R* th = reinterpret_cast<R*>(smem_raw + sizeof(TeamSmem<R>) * WPB);
+    load_theta(A, th);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    TeamSmem<R>& sm = sms[w];
+    const int64_t team = (int64_t)blockIdx.x * WPB + w;
+    R* Cs = A.scratch + team * A.team_stride;
+    WarpTeam tm;
+    for (;;) {
+        unsigned long long wi = 0;
+        if (lane == 0) wi = atomicAdd(A.counter, 1ull);
+        wi = __shfl_sync(0xffffffffu, wi, 0);
+        if ((int64_t)wi >= A.n_work) break;
+        aca_block<R, KIND>(A, tm, sm, th, Cs, A.work[wi], mode);
+    }
+}
+
+template <typename R, int KIND>
+__global__ void __launch_bounds__(CTA_T) k_aca_cta(AcaArgs<R> A, int mode)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TeamSmem<R>& sm = *reinterpret_cast<TeamSmem<R>*>(smem_raw);
+    R* th = reinterpret_cast<R*>(smem_raw + sizeof(TeamSmem<R>));
+    __shared__ unsigned long long wi_s;
+    load_theta(A, th);
+    R* Cs = A.scratch + (int64_t)blockIdx.x * A.team_stride;
+    CtaTeam tm;
+    for (;;) {
+        if (threadIdx.x == 0) wi_s = atomicAdd(A.counter, 1ull);
+        __syncthreads();
+        unsigned long long wi = wi_s;
+        __syncthreads();
+        if ((int64_t)wi >= A.n_work) break;
+        aca_block<R, KIND>(A, tm, sm, th, Cs, A.work[wi], mode);
+    }
+}
+
+// ---- work lists --------------------------------------------------------------
+__global__ void k_classify_blocks(const int32_t* __restrict__ PG, int64_t nG, const int32_t* __restrict__ nbeg,
+                                  const int32_t* __restrict__ nend, int shard, int n_shards,
+                                  int64_t* __restrict__ small_flag, int64_t* __restrict__ large_flag,
+                                  uint64_t* __restrict__ large_key)
+{
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nG) return;
+    int32_t c = nend[PG[2 * b]] - nbeg[PG[2 * b]], q = nend[PG[2 * b + 1]] - nbeg[PG[2 * b + 1]];
+    bool mine = (b % n_shards) == shard;
+    bool small = c <= SMALL_MAX && q <= SMALL_MAX;
+    small_flag[b] = mine && small;
+    large_flag[b] = mine && !small;
+    // larger blocks first: key = (2^31 - 1 - (c + q)) << 32 | b
+    large_key[b] = ((uint64_t)(0x7fffffffu - (uint32_t)(c + q)) << 32) | (uint64_t)b;
+}
+
+__global__ void k_compact(const int64_t* __restrict__ flag, const int64_t* __restrict__ off, int64_t n,
+                          int32_t* __restrict__ out)
+{
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n && flag[b]) out[off[b]] = (int32_t)b;
+}
+
+__global__ void k_compact_keys(const int64_t* __restrict__ flag, const int64_t* __restrict__ off,
+                               const uint64_t* __restrict__ key, int64_t n, uint64_t* __restrict__ out)
+{
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < n && flag[b]) out[off[b]] = key[b];
+}
+
+__global__ void k_keys_to_work(const uint64_t* __restrict__ key, int64_t n, int32_t* __restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (int32_t)(key[i] & 0xffffffffu);
+}
+
+__global__ void k_max_dim(const int32_t* __restrict__ work, int64_t n, const int32_t* __restrict__ PG,
+                          const int32_t* __restrict__ nbeg, const int32_t* __restrict__ nend, int* out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t b = work[i];
+    int32_t c = nend[PG[2 * b]] - nbeg[PG[2 * b]], q = nend[PG[2 * b + 1]] - nbeg[PG[2 * b + 1]];
+    atomicMax(out, c + q);
+}
+
+template <typename R, int KIND>
+void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_small, const int32_t* work_large,
+                int64_t n_large, int max_large_cq, int mode, cudaStream_t s)
+{
+    const int th_bytes = A.n_th * (int)sizeof(R);
+    const int mr = std::min(A.max_rank, MAXR);
+    // large blocks first (CTA teams), then small blocks (warp teams)
+    if (n_large > 0) {
+        // factors (max_rank x 9 x (c+q) reals) + c+q flag bytes, rounded to 256 B
+        int64_t stride = (int64_t)max_large_cq * 9 * mr + ceil_div(max_large_cq, (int64_t)sizeof(R));
+        stride = ceil_div(stride * (int64_t)sizeof(R), 256) * 256 / (int64_t)sizeof(R);
+        const int64_t budget = (int64_t)24 << 30;  // bytes of large-team workspace
+        int64_t teams = std::min<int64_t>(n_large, 2 * ctx->n_sm);
+        teams = std::max<int64_t>(1, std::min<int64_t>(teams, budget / (stride * (int64_t)sizeof(R))));
+        R* scratch = dev_alloc_t<R>(stride * teams, s);
+        HH_CUDA(cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), s));
+        AcaArgs<R> B = A;
+        B.work = work_large;
+        B.n_work = n_large;
+        B.scratch = scratch;
+        B.team_stride = stride;
+        size_t smem = sizeof(TeamSmem<R>) + th_bytes;
+        HH_CUDA(cudaFuncSetAttribute(k_aca_cta<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_aca_cta<R, KIND><<<(unsigned)teams, CTA_T, smem, s>>>(B, mode);
+        HH_CHECK_LAUNCH();
+        dev_free(scratch, s);
+    }
+    if (n_small > 0) {
+        int64_t blocks = std::min<int64_t>(ceil_div(n_small, WPB), 4 * ctx->n_sm);
+        int64_t teams = blocks * WPB;
+        int64_t stride = (int64_t)2 * SMALL_MAX * 9 * mr;
+        R* scratch = dev_alloc_t<R>(stride * teams, s);
+        HH_CUDA(cudaMemsetAsync(A.counter + 1, 0, sizeof(unsigned long long), s));
+        AcaArgs<R> B = A;
+        B.work = work_small;
+        B.n_work = n_small;
+        B.counter = A.counter + 1;
+        B.scratch = scratch;
+        B.team_stride = stride;
+        size_t smem = WPB * sizeof(TeamSmem<R>) + th_bytes;
+        HH_CUDA(cudaFuncSetAttribute(k_aca_warp<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_aca_warp<R, KIND><<<(unsigned)blocks, 32 * WPB, smem, s>>>(B, mode);
+        HH_CHECK_LAUNCH();
+        dev_free(scratch, s);
+    }
+}
+
+// ---- low-rank apply from stored factors ------------------------------------
+// transpose = 0: y_tau(m) = sum_p C_p(m) (sum_n Q_p(n) F(n))
+// transpose = 1: y_sigma(n) = sum_p Q_p(n)^T (sum_m C_p(m)^T W(m))
+template <typename R>
+__global__ void __launch_bounds__(128) k_apply(const R* __restrict__ fac, const int64_t* __restrict__ fofs,
+                                               const int32_t* __restrict__ rank, const int32_t* __restrict__ PG,
+                                               int64_t nG, const int32_t* __restrict__ nbeg,
+                                               const int32_t* __restrict__ nend, const double* __restrict__ Fs,
+                                               R* __restrict__ part, const int64_t* __restrict__ pofs, int transpose)
+{
+    __shared__ R tv[4][MAXR * 3];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t b = (int64_t)blockIdx.x * 4 + w;
+    if (b >= nG) return;
+    const int32_t t = PG[2 * b], s = PG[2 * b + 1];
+    const int32_t t0 = nbeg[t], c = nend[t] - t0, s0 = nbeg[s], q = nend[s] - s0;
+    const int l = rank[b];
+    const R* Cs = fac + 9 * fofs[b];
+    const R* Qs = Cs + (int64_t)l * 9 * c;
+    const int nin = transpose ? c : q, nout = transpose ? q : c;
+    const int in0 = transpose ? t0 : s0;
+    const R* Fin = transpose ? Cs : Qs;
+    const R* Fout = transpose ? Qs : Cs;
+    for (int p = 0; p < l; ++p) {
+        const R* Mp = Fin + (int64_t)p * 9 * nin;
+        R a0 = 0, a1 = 0, a2 = 0;
+        for (int x = lane; x < nin; x += 32) {
+            R v[9];
+            ld9(Mp, nin, x, v);
+            const double* f = Fs + 3 * (int64_t)(in0 + x);
+            R f0 = (R)f[0], f1 = (R)f[1], f2 = (R)f[2];
+            if (!transpose) {
+                a0 += v[0] * f0 + v[1] * f1 + v[2] * f2;
+                a1 += v[3] * f0 + v[4] * f1 + v[5] * f2;
+                a2 += v[6] * f0 + v[7] * f1 + v[8] * f2;
+            } else {  // C_p(m)^T w(m)
+                a0 += v[0] * f0 + v[3] * f1 + v[6] * f2;
+                a1 += v[1] * f0 + v[4] * f1 + v[7] * f2;
+                a2 += v[2] * f0 + v[5] * f1 + v[8] * f2;
+            }
+        }
+        a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2);
+        if (lane == 0) { tv[w][3 * p] = a0; tv[w][3 * p + 1] = a1; tv[w][3 * p + 2] = a2; }
+    }
+    __syncwarp();
+    R* out = part + 3 * pofs[b];
+    for (int x = lane; x < nout; x += 32) {
+        R y0 = 0, y1 = 0, y2 = 0;
+        for (int p = 0; p < l; ++p) {
+            R v[9];
+            ld9(Fout + (int64_t)p * 9 * nout, nout, x, v);
+            const R* tp = tv[w] + 3 * p;
+            if (!transpose) {
+                y0 += v[0] * tp[0] + v[1] * tp[1] + v[2] * tp[2];
+                y1 += v[3] * tp[0] + v[4] * tp[1] + v[5] * tp[2];
+                y2 += v[6] * tp[0] + v[7] * tp[1] + v[8] * tp[2];
+            } else {  // Q_p(n)^T s_p
+                y0 += v[0] * tp[0] + v[3] * tp[1] + v[6] * tp[2];
+                y1 += v[1] * tp[0] + v[4] * tp[1] + v[7] * tp[2];
+                y2 += v[2] * tp[0] + v[5] * tp[1] + v[8] * tp[2];
+            }
+        }
+        out[3 * x] = y0; out[3 * x + 1] = y1; out[3 * x + 2] = y2;
+    }
+}
+
+template <typename R>
+void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_params& p, const AcaRun& r,
+               cudaStream_t s)
+{
+    const int64_t nG = bl->nG;
+    if (nG == 0) return;
+    HH_REQUIRE(p.max_rank >= 1 && p.max_rank <= MAXR, HH_ERR_ARG, "max_rank must be in [1, 64]");
+    AcaArgs<R> A{};
+    A.Xs = t->Xs;
+    A.th_g = theta_for<R>(ctx, p, &A.n_th);
+    A.pp = PairParams{p.radius, p.viscosity};
+    A.Fs = r.Fs;
+    A.PG = bl->PG;
+    A.nbeg = t->nbeg;
+    A.nend = t->nend;
+    A.counter = ctx->d_counters;
+    A.max_rank = p.max_rank;
+    A.eps2 = p.eps * p.eps;
+    A.j1_rule = p.j1_rule;
+    A.seed = p.seed;
+    A.rank = r.rank;
+    A.pivI = r.pivI;
+    A.pivJ = r.pivJ;
+    A.part = (R*)r.part;
+    A.pofs = r.pofs;
+    A.fac = (R*)r.factors;
+    A.fofs = r.fofs;
+    A.status = ctx->d_status;
+    A.n_queries = ctx->d_counters + 4;
+
+    // work lists: small blocks in block order, large blocks by decreasing c + q
+    int64_t* fs = dev_alloc_t<int64_t>(nG, s);
+    int64_t* fl = dev_alloc_t<int64_t>(nG, s);
+    int64_t* os = dev_alloc_t<int64_t>(nG, s);
+    int64_t* ol = dev_alloc_t<int64_t>(nG, s);
+    uint64_t* key = dev_alloc_t<uint64_t>(nG, s);
+    int64_t* tot = dev_alloc_t<int64_t>(2, s);
+    k_classify_blocks<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(bl->PG, nG, t->nbeg, t->nend, p.shard_id,
+                                                                  p.n_shards, fs, fl, key);
+    HH_CHECK_LAUNCH();
+    dev_scan_i64(fs, os, nG, tot, s);
+    dev_scan_i64(fl, ol, nG, tot + 1, s);
+    int64_t h[2];
+    HH_CUDA(cudaMemcpyAsync(h, tot, sizeof h, cudaMemcpyDeviceToHost, s));
+    HH_CUDA(cudaStreamSynchronize(s));
+    int32_t* ws = dev_alloc_t<int32_t>(h[0], s);
+    int32_t* wl = dev_alloc_t<int32_t>(h[1], s);
+    k_compact<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(fs, os, nG, ws);
+    HH_CHECK_LAUNCH();
+    int max_cq = 0;
+    if (h[1] > 0) {
+        uint64_t* lk = dev_alloc_t<uint64_t>(h[1], s);
+        k_compact_keys<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(fl, ol, key, nG, lk);
+        HH_CHECK_LAUNCH();
+        dev_radix_sort(lk, nullptr, h[1], 64, s);
+        k_keys_to_work<<<(unsigned)ceil_div(h[1], 256), 256, 0, s>>>(lk, h[1], wl);
+        HH_CHECK_LAUNCH();
+        dev_free(lk, s);
+        int* dmax = dev_alloc_t<int>(1, s);
+        HH_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), s));
+        k_max_dim<<<(unsigned)ceil_div(h[1], 256), 256, 0, s>>>(wl, h[1], bl->PG, t->nbeg, t->nend, dmax);
+        HH_CHECK_LAUNCH();
+        HH_CUDA(cudaMemcpyAsync(&max_cq, dmax, sizeof(int), cudaMemcpyDeviceToHost, s));
+        HH_CUDA(cudaStreamSynchronize(s));
+        dev_free(dmax, s);
+    }
+    const int kind = kernel_kind(p, ctx->width);
+    if (kind == 0) launch_aca<R, 0>(ctx, A, ws, h[0], wl, h[1], max_cq, r.mode, s);
+    else if (kind == 1) launch_aca<R, 1>(ctx, A, ws, h[0], wl, h[1], max_cq, r.mode, s);
+    else launch_aca<R, 2>(ctx, A, ws, h[0], wl, h[1], max_cq, r.mode, s);
+    dev_free(fs, s); dev_free(fl, s); dev_free(os, s); dev_free(ol, s); dev_free(key, s); dev_free(tot, s);
+    dev_free(ws, s); dev_free(wl, s);
+}
+
+}  // namespace
+
+void aca_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_params& p, const AcaRun& r, cudaStream_t s)
+{
+    if (p.precision == HH_FP64) aca_run_t<double>(ctx, t, b, p, r, s);
+    else aca_run_t<float>(ctx, t, b, p, r, s);
+}
+
+void lowrank_apply(hh_ctx* ctx, const hh_hmat* h, const double* Fs, void* part, const int64_t* pofs, int transpose,
+                   cudaStream_t s)
+{
+    (void)ctx;
+    const int64_t nG = h->blocks->nG;
+    if (nG == 0) return;
+    const unsigned grid = (unsigned)ceil_div(nG, 4);
+    if (h->real_bytes == 8)
+        k_apply<double><<<grid, 128, 0, s>>>((const double*)h->factors, h->fofs, h->rank, h->blocks->PG, nG,
+                                             h->tree->nbeg, h->tree->nend, Fs, (double*)part, pofs, transpose);
+    else
+        k_apply<float><<<grid, 128, 0, s>>>((const float*)h->factors, h->fofs, h->rank, h->blocks->PG, nG,
+                                            h->tree->nbeg, h->tree->nend, Fs, (float*)part, pofs, transpose);
+    HH_CHECK_LAUNCH();
+}

@@ -1,0 +1,518 @@
+// hh_api.cu -- the C-ABI of libhhignn (declared in include/hhignn.h).
+//
+// Orchestrates the stages of one H-matrix mobility product:
+//   tree (Definition 1) -> partition (Eq. 7, Algorithm 1) -> ACA on P^G
+//   (Algorithm 2) -> dense P^H blocks -> FP64 accumulation of Eq. 6.
+// Every entry point catches the library's internal errors and turns them
+// into an hh_status plus a message for hh_last_error().
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "hh_internal.h"
+
+namespace {
+
+constexpr int kMaxTheta = 16384;
+
+__global__ void k_widen(const float* __restrict__ in, double* __restrict__ out, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)in[i];
+}
+
+// Packed layout (W [out,in], b per layer) -> the SIMT layout of mlp_f32:
+// W1t [4][w], b1, W2t [w][w], b2, W3t [w][w], b3, W4t [w][8] (zero pad), b4 [8].
+__global__ void k_transpose_theta(const float* __restrict__ in, float* __restrict__ out, int w)
+{
+    const int dims[5] = {4, w, w, w, 6};
+    int src = 0, dst = 0;
+    for (int l = 0; l < 4; ++l) {
+        const int ni = dims[l], no = dims[l + 1], nop = (l == 3) ? 8 : no;
+        for (int x = threadIdx.x; x < ni * nop; x += blockDim.x) {
+            const int i = x / nop, o = x % nop;
+            out[dst + x] = o < no ? in[src + o * ni + i] : 0.0f;
+        }
+        for (int o = threadIdx.x; o < nop; o += blockDim.x) out[dst + ni * nop + o] = o < no ? in[src + ni * no + o] : 0.0f;
+        src += ni * no + no;
+        dst += ni * nop + nop;
+    }
+}
+
+double alpha1(const hh_params& p) { return 1.0 / (6.0 * HH_PI * p.viscosity * p.radius); }
+
+void check_params(const hh_ctx* ctx, const hh_params* p)
+{
+    HH_REQUIRE(p != nullptr, HH_ERR_ARG, "params is NULL");
+    HH_REQUIRE(p->leaf_size >= 2 && p->leaf_size <= 129, HH_ERR_ARG, "leaf_size must be in [2, 129]");
+    HH_REQUIRE(p->eta > 0.0, HH_ERR_ARG, "eta must be > 0");
+    HH_REQUIRE(p->eps >= 0.0, HH_ERR_ARG, "eps must be >= 0");
+    HH_REQUIRE(p->max_rank >= 1 && p->max_rank <= 64, HH_ERR_ARG, "max_rank must be in [1, 64]");
+    HH_REQUIRE(p->precision == HH_FP64 || p->precision == HH_FP32 || p->precision == HH_BF16, HH_ERR_ARG,
+               "unknown precision");
+    HH_REQUIRE(p->precision != HH_BF16, HH_ERR_ARG, "precision HH_BF16 is not available in this build");
+    HH_REQUIRE(p->kernel == HH_MLP || p->kernel == HH_RPY, HH_ERR_ARG, "unknown kernel");
+    HH_REQUIRE(p->kernel == HH_RPY || ctx->n_theta > 0, HH_ERR_ARG, "MLP kernel requested but hh_set_mlp not called");
+    HH_REQUIRE(p->radius > 0.0 && p->viscosity > 0.0, HH_ERR_ARG, "radius and viscosity must be > 0");
+    HH_REQUIRE(p->n_shards >= 1 && p->shard_id >= 0 && p->shard_id < p->n_shards, HH_ERR_ARG, "bad shard");
+    HH_REQUIRE(p->j1_rule == 0 || p->j1_rule == 1, HH_ERR_ARG, "j1_rule must be 0 or 1");
+}
+
+template <typename F>
+hh_status guarded(hh_ctx* ctx, F&& f)
+{
+    try {
+        hh_status st = f();
+        if (ctx) ctx->err.clear();
+        return st;
+    } catch (const HHError& e) {
+        if (ctx) ctx->err = e.msg;
+        return e.st;
+    } catch (const std::bad_alloc&) {
+        if (ctx) ctx->err = "host allocation failed";
+        return HH_ERR_OOM;
+    }
+}
+
+void reset_call(hh_ctx* ctx, cudaStream_t s)
+{
+    HH_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s));
+    HH_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 8 * sizeof(unsigned long long), s));
+    ctx->last_stream = s;
+}
+
+hh_status read_status(hh_ctx* ctx, cudaStream_t s)
+{
+    unsigned st = 0;
+    HH_CUDA(cudaMemcpyAsync(&st, ctx->d_status, sizeof st, cudaMemcpyDeviceToHost, s));
+    HH_CUDA(cudaStreamSynchronize(s));
+    HH_CUDA(cudaGetLastError());
+    if (st & HH_DEV_TIMEOUT) throw HHError{HH_ERR_TIMEOUT, "a bounded device wait gave up"};
+    if (st & HH_DEV_NUMERIC) throw HHError{HH_ERR_NUMERIC, "non-finite input"};
+    return (st & HH_DEV_RANK_CAP) ? HH_WARN_RANK_CAP : HH_OK;
+}
+
+__global__ void k_rank_hist(const int32_t* __restrict__ rank, int64_t n, unsigned long long* hist)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&hist[min(rank[i], 64)], 1ull);
+}
+
+__global__ void k_fac_len(const int32_t* __restrict__ PG, int64_t nG, const int32_t* __restrict__ nbeg,
+                          const int32_t* __restrict__ nend, const int32_t* __restrict__ rank, int64_t* __restrict__ len)
+{
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nG) {
+        int32_t t = PG[2 * b], s = PG[2 * b + 1];
+        len[b] = (int64_t)(nend[t] - nbeg[t] + nend[s] - nbeg[s]) * rank[b];
+    }
+}
+
+}  // namespace
+
+void free_hmat(hh_hmat* h)
+{
+    if (!h) return;
+    cudaFree(h->rank); cudaFree(h->pivI); cudaFree(h->pivJ); cudaFree(h->fofs); cudaFree(h->factors);
+    delete h;
+}
+
+extern "C" {
+
+void hh_default_params(hh_params* p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->leaf_size = 32;
+    p->eta = 1.0;
+    p->eps = 1e-4;
+    p->max_rank = 48;
+    p->precision = HH_FP32;
+    p->kernel = HH_MLP;
+    p->radius = 1.0;
+    p->viscosity = 1.0;
+    p->j1_rule = 0;
+    p->seed = 0;
+    p->shard_id = 0;
+    p->n_shards = 1;
+    p->flags = 0;
+}
+
+hh_status hh_create(hh_ctx** out, int device)
+{
+    if (!out) return HH_ERR_ARG;
+    *out = nullptr;
+    hh_ctx* ctx = new hh_ctx();
+    int prev = 0;
+    cudaGetDevice(&prev);
+    hh_status st = guarded(ctx, [&]() {
+        int n = 0;
+        HH_CUDA(cudaGetDeviceCount(&n));
+        HH_REQUIRE(device >= 0 && device < n, HH_ERR_ARG, "no such device");
+        HH_CUDA(cudaSetDevice(device));
+        ctx->device = device;
+        HH_CUDA(cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device));
+        cudaMemPool_t pool;
+        HH_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+        uint64_t thr = UINT64_MAX;
+        HH_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+        HH_CUDA(cudaMalloc(&ctx->d_status, sizeof(unsigned)));
+        HH_CUDA(cudaMalloc(&ctx->d_counters, 8 * sizeof(unsigned long long)));
+        HH_CUDA(cudaMemset(ctx->d_status, 0, sizeof(unsigned)));
+        HH_CUDA(cudaMemset(ctx->d_counters, 0, 8 * sizeof(unsigned long long)));
+        for (auto& e : ctx->ev) HH_CUDA(cudaEventCreate(&e));
+        return HH_OK;
+    });
+    cudaSetDevice(prev);
+    if (st != HH_OK) {
+        fprintf(stderr, "hh_create: %s\n", ctx->err.c_str());
+        hh_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return HH_OK;
+}
+
+void hh_destroy(hh_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaFree(ctx->theta32);
+    cudaFree(ctx->theta32t);
+    cudaFree(ctx->theta64);
+    cudaFree(ctx->d_status);
+    cudaFree(ctx->d_counters);
+    for (auto& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+}
+
+const char* hh_last_error(const hh_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+hh_status hh_set_mlp(hh_ctx* ctx, const float* theta_dev, int width, int depth, void* stream)
+{
+    if (!ctx) return HH_ERR_ARG;
+    return guarded(ctx, [&]() {
+        HH_REQUIRE(theta_dev != nullptr, HH_ERR_ARG, "theta is NULL");
+        HH_REQUIRE(depth == 3, HH_ERR_ARG, "depth must be 3 (4 -> w -> w -> w -> 6)");
+        HH_REQUIRE(width == 32 || width == 64, HH_ERR_ARG, "width must be 32 or 64");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int n = 4 * width + width + 2 * (width * width + width) + 6 * width + 6;
+        HH_REQUIRE(n <= kMaxTheta, HH_ERR_ARG, "too many parameters");
+        const int nt = width == 32 ? mlp_t_size<32>() : mlp_t_size<64>();
+        if (ctx->theta32) {
+            HH_CUDA(cudaDeviceSynchronize());
+            cudaFree(ctx->theta32);
+            cudaFree(ctx->theta32t);
+            cudaFree(ctx->theta64);
+        }
+        ctx->theta32 = nullptr;
+        ctx->theta32t = nullptr;
+        ctx->theta64 = nullptr;
+        HH_CUDA(cudaMalloc(&ctx->theta32, sizeof(float) * n));
+        HH_CUDA(cudaMalloc(&ctx->theta32t, sizeof(float) * nt));
+        HH_CUDA(cudaMalloc(&ctx->theta64, sizeof(double) * n));
+        HH_CUDA(cudaMemcpyAsync(ctx->theta32, theta_dev, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+        k_widen<<<(n + 255) / 256, 256, 0, s>>>(ctx->theta32, ctx->theta64, n);
+        HH_CHECK_LAUNCH();
+        k_transpose_theta<<<1, 256, 0, s>>>(ctx->theta32, ctx->theta32t, width);
+        HH_CHECK_LAUNCH();
+        ctx->width = width;
+        ctx->n_theta = n;
+        ctx->n_theta_t = nt;
+        return HH_OK;
+    });
+}
+
+hh_status hh_build_tree(hh_ctx* ctx, const double* X_dev, const int64_t* offsets, int32_t batch, const hh_params* p,
+                        void* stream, hh_tree** out)
+{
+    if (!ctx || !out) return HH_ERR_ARG;
+    return guarded(ctx, [&]() {
+        check_params(ctx, p);
+        HH_REQUIRE(offsets != nullptr, HH_ERR_ARG, "offsets is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        reset_call(ctx, s);
+        hh_tree* t = build_tree_impl(ctx, X_dev, offsets, batch, *p, s);
+        try {
+            read_status(ctx, s);
+        } catch (...) {
+            free_tree(t);
+            throw;
+        }
+        *out = t;
+        ctx->stats.n_nodes = t->n_nodes;
+        return HH_OK;
+    });
+}
+
+hh_status hh_partition(hh_ctx* ctx, const hh_tree* tree, const hh_params* p, void* stream, hh_blocks** out)
+{
+    if (!ctx || !out || !tree) return HH_ERR_ARG;
+    return guarded(ctx, [&]() {
+        check_params(ctx, p);
+        cudaStream_t s = (cudaStream_t)stream;
+        *out = partition_impl(ctx, tree, *p, s);
+        ctx->stats.n_blocks_G = (*out)->nG;
+        ctx->stats.n_blocks_H = (*out)->nH;
+        return HH_OK;
+    });
+}
+
+hh_status hh_aca(hh_ctx* ctx, const hh_tree* tree, const hh_blocks* blocks, const hh_params* p, void* stream,
+                 hh_hmat** out)
+{
+    if (!ctx || !out || !tree || !blocks) return HH_ERR_ARG;
+    hh_hmat* h = nullptr;
+    hh_status st = guarded(ctx, [&]() {
+        check_params(ctx, p);
+        HH_REQUIRE(blocks->tree == tree, HH_ERR_ARG, "blocks belong to another tree");
+        HH_REQUIRE(p->leaf_size == tree->params.leaf_size && p->eta == blocks->params.eta, HH_ERR_ARG,
+                   "leaf_size / eta differ from the partition's");
+        cudaStream_t s = (cudaStream_t)stream;
+        reset_call(ctx, s);
+        h = new hh_hmat();
+        h->ctx = ctx;
+        h->tree = tree;
+        h->blocks = blocks;
+        h->params = *p;
+        h->real_bytes = real_bytes(*p);
+        const int64_t nG = blocks->nG;
+        const int64_t nGa = nG > 0 ? nG : 1;
+        HH_CUDA(cudaMalloc(&h->rank, sizeof(int32_t) * nGa));
+        HH_CUDA(cudaMalloc(&h->pivI, sizeof(int32_t) * nGa * p->max_rank));
+        HH_CUDA(cudaMalloc(&h->pivJ, sizeof(int32_t) * nGa * p->max_rank));
+        HH_CUDA(cudaMalloc(&h->fofs, sizeof(int64_t) * (nG + 1)));
+        HH_CUDA(cudaMemsetAsync(h->rank, 0, sizeof(int32_t) * nGa, s));
+        HH_CUDA(cudaMemsetAsync(h->pivI, 0xff, sizeof(int32_t) * nGa * p->max_rank, s));
+        HH_CUDA(cudaMemsetAsync(h->pivJ, 0xff, sizeof(int32_t) * nGa * p->max_rank, s));
+        HH_CUDA(cudaMemsetAsync(h->fofs, 0, sizeof(int64_t) * (nG + 1), s));
+        HH_CUDA(cudaEventRecord(ctx->ev[0], s));
+        AcaRun r;
+        r.rank = h->rank;
+        r.pivI = h->pivI;
+        r.pivJ = h->pivJ;
+        r.mode = 1;
+        aca_run(ctx, tree, blocks, *p, r, s);
+        if (nG > 0) {
+            int64_t* len = dev_alloc_t<int64_t>(nG, s);
+            k_fac_len<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(blocks->PG, nG, tree->nbeg, tree->nend, h->rank, len);
+            HH_CHECK_LAUNCH();
+            dev_scan_i64(len, h->fofs, nG, h->fofs + nG, s);
+            HH_CUDA(cudaMemcpyAsync(&h->n_factor, h->fofs + nG, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            HH_CUDA(cudaStreamSynchronize(s));
+            dev_free(len, s);
+        }
+        HH_CUDA(cudaMalloc(&h->factors, (size_t)h->real_bytes * 9 * (h->n_factor > 0 ? h->n_factor : 1)));
+        r.factors = h->factors;
+        r.fofs = h->fofs;
+        r.mode = 2;
+        aca_run(ctx, tree, blocks, *p, r, s);
+        HH_CUDA(cudaEventRecord(ctx->ev[1], s));
+        hh_status w = read_status(ctx, s);
+        float ms = 0.f;
+        HH_CUDA(cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]));
+        ctx->stats.t_aca = ms;
+        unsigned long long* hist = dev_alloc_t<unsigned long long>(65, s);
+        HH_CUDA(cudaMemsetAsync(hist, 0, 65 * sizeof(unsigned long long), s));
+        if (nG > 0) {
+            k_rank_hist<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(h->rank, nG, hist);
+            HH_CHECK_LAUNCH();
+        }
+        unsigned long long hh[65], cnt[8];
+        HH_CUDA(cudaMemcpyAsync(hh, hist, sizeof hh, cudaMemcpyDeviceToHost, s));
+        HH_CUDA(cudaMemcpyAsync(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost, s));
+        HH_CUDA(cudaStreamSynchronize(s));
+        dev_free(hist, s);
+        for (int i = 0; i < 65; ++i) ctx->stats.rank_hist[i] = (int64_t)hh[i];
+        ctx->stats.n_aca_queries = (int64_t)cnt[4] / 2;  // the rank loop ran twice
+        ctx->stats.n_blocks_G = nG;
+        ctx->stats.n_blocks_H = blocks->nH;
+        *out = h;
+        return w;
+    });
+    if (st != HH_OK && st != HH_WARN_RANK_CAP) {
+        free_hmat(h);
+        *out = nullptr;
+    }
+    return st;
+}
+
+hh_status hh_matvec(hh_ctx* ctx, const hh_hmat* h, const double* F_dev, double* U_dev, int transpose, void* stream)
+{
+    if (!ctx || !h) return HH_ERR_ARG;
+    return guarded(ctx, [&]() {
+        HH_REQUIRE(F_dev && U_dev, HH_ERR_ARG, "F or U is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        const hh_tree* t = h->tree;
+        const hh_blocks* b = h->blocks;
+        const hh_params& p = h->params;
+        const int rb = real_bytes(p);
+        double* Fs = dev_alloc_t<double>(3 * t->n, s);
+        gather_rows(F_dev, t->perm, t->n, Fs, s);
+        void* y = dev_alloc(rb * 3 * (size_t)t->n, s);
+        near_field(ctx, t, b, p, Fs, y, transpose, s);
+        int64_t* pofs = dev_alloc_t<int64_t>(b->nG + 1, s);
+        int64_t total = partial_offsets(t, b, transpose, pofs, s);
+        void* part = dev_alloc(rb * 3 * (size_t)(total > 0 ? total : 1), s);
+        lowrank_apply(ctx, h, Fs, part, pofs, transpose, s);
+        int32_t* order = nullptr;
+        int64_t* col = nullptr;
+        if (transpose) {
+            order = dev_alloc_t<int32_t>(b->nG, s);
+            col = dev_alloc_t<int64_t>(t->n_nodes + 1, s);
+            source_index(t, b, order, col, s);
+        }
+        double a1 = p.shard_id == 0 ? alpha1(p) : 0.0;
+        accumulate_impl(ctx, t, p, Fs, y, b->nG > 0 ? part : nullptr, pofs, transpose ? col : b->rowG, order, a1,
+                        U_dev, s);
+        dev_free(order, s);
+        dev_free(col, s);
+        dev_free(part, s);
+        dev_free(pofs, s);
+        dev_free(y, s);
+        dev_free(Fs, s);
+        return HH_OK;
+    });
+}
+
+hh_status hh_predict(hh_ctx* ctx, const double* X_dev, const double* F_dev, const int64_t* offsets, int32_t batch,
+                     const hh_params* p, void* stream, double* U_dev)
+{
+    if (!ctx) return HH_ERR_ARG;
+    hh_tree* t = nullptr;
+    hh_blocks* b = nullptr;
+    hh_status st = guarded(ctx, [&]() {
+        check_params(ctx, p);
+        HH_REQUIRE(offsets != nullptr && F_dev && U_dev && X_dev, HH_ERR_ARG, "NULL argument");
+        cudaStream_t s = (cudaStream_t)stream;
+        reset_call(ctx, s);
+        cudaEvent_t* ev = ctx->ev;
+        HH_CUDA(cudaEventRecord(ev[0], s));
+        t = build_tree_impl(ctx, X_dev, offsets, batch, *p, s);
+        read_status(ctx, s);  // stop early on non-finite positions
+        HH_CUDA(cudaEventRecord(ev[1], s));
+        b = partition_impl(ctx, t, *p, s);
+        HH_CUDA(cudaEventRecord(ev[2], s));
+        const int rb = real_bytes(*p);
+        double* Fs = dev_alloc_t<double>(3 * t->n, s);
+        gather_rows(F_dev, t->perm, t->n, Fs, s);
+        void* y = dev_alloc(rb * 3 * (size_t)t->n, s);
+        near_field(ctx, t, b, *p, Fs, y, 0, s);
+        HH_CUDA(cudaEventRecord(ev[3], s));
+        int64_t* pofs = dev_alloc_t<int64_t>(b->nG + 1, s);
+        int64_t total = partial_offsets(t, b, 0, pofs, s);
+        void* part = dev_alloc(rb * 3 * (size_t)(total > 0 ? total : 1), s);
+        AcaRun r;
+        r.Fs = Fs;
+        r.part = part;
+        r.pofs = pofs;
+        r.mode = 0;
+        aca_run(ctx, t, b, *p, r, s);
+        HH_CUDA(cudaEventRecord(ev[4], s));
+        double a1 = p->shard_id == 0 ? alpha1(*p) : 0.0;
+        accumulate_impl(ctx, t, *p, Fs, y, b->nG > 0 ? part : nullptr, pofs, b->rowG, nullptr, a1, U_dev, s);
+        HH_CUDA(cudaEventRecord(ev[5], s));
+        dev_free(part, s);
+        dev_free(pofs, s);
+        dev_free(y, s);
+        dev_free(Fs, s);
+        hh_status w = read_status(ctx, s);
+        float ms[5];
+        for (int i = 0; i < 5; ++i) HH_CUDA(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
+        ctx->stats.t_tree = ms[0];
+        ctx->stats.t_part = ms[1];
+        ctx->stats.t_near = ms[2];
+        ctx->stats.t_aca = ms[3];
+        ctx->stats.t_apply = 0.0;
+        ctx->stats.t_acc = ms[4];
+        ctx->stats.n_nodes = t->n_nodes;
+        ctx->stats.n_blocks_G = b->nG;
+        ctx->stats.n_blocks_H = b->nH;
+        unsigned long long cnt[8];
+        HH_CUDA(cudaMemcpy(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost));
+        ctx->stats.n_aca_queries = (int64_t)cnt[4];
+        ctx->stats.n_near_pairs = (int64_t)cnt[5];
+        return w;
+    });
+    free_blocks(b);
+    free_tree(t);
+    return st;
+}
+
+hh_status hh_matvec_backward(hh_ctx* ctx, const hh_hmat* h, const double* gU_dev, const double* F_dev, double* gF_dev,
+                             double* gX_dev, float* gtheta_dev, void* stream)
+{
+    if (!ctx || !h) return HH_ERR_ARG;
+    return guarded(ctx, [&]() -> hh_status {
+        (void)gU_dev; (void)F_dev; (void)gF_dev; (void)gX_dev; (void)gtheta_dev; (void)stream;
+        throw HHError{HH_ERR_ARG, "hh_matvec_backward is not available in this build"};
+    });
+}
+
+hh_status hh_export_tree(const hh_tree* t, int32_t* perm, uint64_t* codes, int32_t* node_begin, int32_t* node_end,
+                         int32_t* node_child, double* node_lo, double* node_hi, int64_t* n_nodes, int64_t* n)
+{
+    if (!t) return HH_ERR_ARG;
+    return guarded(t->ctx, [&]() {
+        HH_CUDA(cudaDeviceSynchronize());
+        if (perm) HH_CUDA(cudaMemcpy(perm, t->perm, sizeof(int32_t) * t->n, cudaMemcpyDeviceToHost));
+        if (codes) HH_CUDA(cudaMemcpy(codes, t->codes, sizeof(uint64_t) * t->n, cudaMemcpyDeviceToHost));
+        if (node_begin) HH_CUDA(cudaMemcpy(node_begin, t->nbeg, sizeof(int32_t) * t->n_nodes, cudaMemcpyDeviceToHost));
+        if (node_end) HH_CUDA(cudaMemcpy(node_end, t->nend, sizeof(int32_t) * t->n_nodes, cudaMemcpyDeviceToHost));
+        if (node_child)
+            HH_CUDA(cudaMemcpy(node_child, t->child, sizeof(int32_t) * 2 * t->n_nodes, cudaMemcpyDeviceToHost));
+        if (node_lo) HH_CUDA(cudaMemcpy(node_lo, t->lo, sizeof(double) * 3 * t->n_nodes, cudaMemcpyDeviceToHost));
+        if (node_hi) HH_CUDA(cudaMemcpy(node_hi, t->hi, sizeof(double) * 3 * t->n_nodes, cudaMemcpyDeviceToHost));
+        if (n_nodes) *n_nodes = t->n_nodes;
+        if (n) *n = t->n;
+        return HH_OK;
+    });
+}
+
+hh_status hh_export_blocks(const hh_blocks* b, int32_t* PG, int64_t* nG, int32_t* PH, int64_t* nH)
+{
+    if (!b) return HH_ERR_ARG;
+    return guarded(b->tree->ctx, [&]() {
+        HH_CUDA(cudaDeviceSynchronize());
+        if (PG && b->nG) HH_CUDA(cudaMemcpy(PG, b->PG, sizeof(int32_t) * 2 * b->nG, cudaMemcpyDeviceToHost));
+        if (PH && b->nH) HH_CUDA(cudaMemcpy(PH, b->PH, sizeof(int32_t) * 2 * b->nH, cudaMemcpyDeviceToHost));
+        if (nG) *nG = b->nG;
+        if (nH) *nH = b->nH;
+        return HH_OK;
+    });
+}
+
+hh_status hh_export_aca(const hh_hmat* h, int32_t* ranks, int32_t* piv_rows, int32_t* piv_cols, int64_t* nG,
+                        int32_t* max_rank)
+{
+    if (!h) return HH_ERR_ARG;
+    return guarded(h->ctx, [&]() {
+        HH_CUDA(cudaDeviceSynchronize());
+        const int64_t n = h->blocks->nG;
+        if (ranks && n) HH_CUDA(cudaMemcpy(ranks, h->rank, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+        if (piv_rows && n)
+            HH_CUDA(cudaMemcpy(piv_rows, h->pivI, sizeof(int32_t) * n * h->params.max_rank, cudaMemcpyDeviceToHost));
+        if (piv_cols && n)
+            HH_CUDA(cudaMemcpy(piv_cols, h->pivJ, sizeof(int32_t) * n * h->params.max_rank, cudaMemcpyDeviceToHost));
+        if (nG) *nG = n;
+        if (max_rank) *max_rank = h->params.max_rank;
+        return HH_OK;
+    });
+}
+
+hh_status hh_stats(hh_ctx* ctx, hh_stats_t* out)
+{
+    if (!ctx || !out) return HH_ERR_ARG;
+    return guarded(ctx, [&]() {
+        *out = ctx->stats;
+        return HH_OK;
+    });
+}
+
+void hh_tree_free(hh_tree* t) { free_tree(t); }
+void hh_blocks_free(hh_blocks* b) { free_blocks(b); }
+void hh_hmat_free(hh_hmat* h) { free_hmat(h); }
+
+}  // extern "C"

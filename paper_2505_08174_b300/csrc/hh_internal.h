@@ -1,0 +1,148 @@
+// hh_internal.h -- host-side object layout and cross-file entry points of
+// libhhignn.  Not part of the public C-ABI (include/hhignn.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hhignn.h"
+#include "hh_common.cuh"
+
+struct hh_ctx {
+    int device = 0;
+    int n_sm = 148;
+    std::string err;
+    float* theta32 = nullptr;   // device copy of the MLP parameters (float32, packed layout)
+    float* theta32t = nullptr;  // transposed, padded FP32 layout read by the SIMT kernels
+    double* theta64 = nullptr;  // packed layout widened to FP64 (FP64 mode)
+    int width = 0, n_theta = 0, n_theta_t = 0;
+    unsigned* d_status = nullptr;              // device status word (HH_DEV_* bits)
+    unsigned long long* d_counters = nullptr;  // [8]: 0,1 work counters; 4 ACA queries; 5 near pairs
+    hh_stats_t stats{};
+    cudaStream_t last_stream = nullptr;
+    cudaEvent_t ev[8] = {};
+};
+
+struct hh_tree {
+    hh_ctx* ctx = nullptr;
+    hh_params params{};
+    int64_t n = 0;
+    int32_t batch = 0;
+    std::vector<int64_t> offsets;    // host copy [batch+1]
+    int64_t* d_offsets = nullptr;    // [batch+1]
+    int32_t* perm = nullptr;         // [n] sorted position -> caller row
+    uint64_t* codes = nullptr;       // [n] sorted Morton codes
+    double* Xs = nullptr;            // [n,3] positions in sorted order
+    int32_t n_nodes = 0;
+    int32_t* nbeg = nullptr;         // [n_nodes]
+    int32_t* nend = nullptr;
+    int32_t* child = nullptr;        // [n_nodes,2], -1 for leaves
+    int32_t* parent = nullptr;
+    double* lo = nullptr;            // [n_nodes,3]
+    double* hi = nullptr;
+    std::vector<int32_t> level_start;  // BFS level boundaries (host)
+};
+
+struct hh_blocks {
+    const hh_tree* tree = nullptr;
+    hh_params params{};
+    int64_t nG = 0, nH = 0;
+    int32_t* PG = nullptr;     // [nG,2] (target, source)
+    int32_t* PH = nullptr;     // [nH,2]
+    int64_t* rowG = nullptr;   // [n_nodes+1]: blocks of target t are rowG[t] .. rowG[t+1]
+    int64_t* rowH = nullptr;
+};
+
+struct hh_hmat {
+    hh_ctx* ctx = nullptr;
+    const hh_tree* tree = nullptr;
+    const hh_blocks* blocks = nullptr;
+    hh_params params{};
+    int32_t* rank = nullptr;   // [nG]
+    int32_t* pivI = nullptr;   // [nG, max_rank]
+    int32_t* pivJ = nullptr;
+    int64_t* fofs = nullptr;   // [nG+1] factor offsets in elements of 9 reals ((c+q) * rank)
+    void* factors = nullptr;   // per block: C [rank][9][c] then Q [rank][9][q]
+    int64_t n_factor = 0;      // total elements
+    int real_bytes = 4;
+};
+
+// --- primitives (hh_prims.cu) ------------------------------------------------
+// Exclusive prefix sum of n int64 values; total (optional) receives the sum
+// on the device.  in and out must not alias.
+void dev_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total, cudaStream_t s);
+// Stable LSD radix sort of (keys, vals) by the low key_bits bits of keys;
+// vals may be NULL.  Sorted data is returned in keys/vals.
+void dev_radix_sort(uint64_t* keys, int32_t* vals, int64_t n, int key_bits, cudaStream_t s);
+// Stream-ordered allocation helpers.
+void* dev_alloc(size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+template <typename T>
+T* dev_alloc_t(int64_t n, cudaStream_t s) { return (T*)dev_alloc(sizeof(T) * (size_t)(n > 0 ? n : 1), s); }
+
+// --- stages ----------------------------------------------------------------
+hh_tree* build_tree_impl(hh_ctx* ctx, const double* X, const int64_t* offsets, int32_t batch, const hh_params& p,
+                         cudaStream_t s);
+hh_blocks* partition_impl(hh_ctx* ctx, const hh_tree* t, const hh_params& p, cudaStream_t s);
+void free_tree(hh_tree* t);
+void free_blocks(hh_blocks* b);
+void free_hmat(hh_hmat* h);
+// order[k]: admissible blocks sorted by (source, target); col[s]: first entry
+// of source node s in order.
+void source_index(const hh_tree* t, const hh_blocks* b, int32_t* order, int64_t* col, cudaStream_t s);
+
+// Gather rows of an [n,3] FP64 array into sorted order: out[m] = in[perm[m]].
+void gather_rows(const double* in, const int32_t* perm, int64_t n, double* out, cudaStream_t s);
+
+// Near field (inadmissible blocks, self pair skipped): y[m] (sorted order,
+// real type of the precision) = sum over P^H of K(x_m - x_n) F_n
+// (transpose: K(x_n - x_m) F_n; the kernels' 3x3 blocks are symmetric).
+void near_field(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_params& p, const double* Fs,
+                void* y, int transpose, cudaStream_t s);
+
+// ACA over admissible blocks.  mode 0: fused apply into per-block partials
+// (part, at 3*pofs[b]); mode 1: ranks + pivots only; mode 2: also write
+// factors at fofs.
+struct AcaRun {
+    const double* Fs = nullptr;   // sorted forces (mode 0)
+    void* part = nullptr;         // per-block partial outputs (mode 0)
+    const int64_t* pofs = nullptr;
+    int32_t* rank = nullptr;
+    int32_t* pivI = nullptr;
+    int32_t* pivJ = nullptr;
+    void* factors = nullptr;
+    const int64_t* fofs = nullptr;
+    int mode = 0;
+};
+void aca_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_params& p, const AcaRun& r,
+             cudaStream_t s);
+
+// Low-rank apply from stored factors into per-block partials.
+void lowrank_apply(hh_ctx* ctx, const hh_hmat* h, const double* Fs, void* part, const int64_t* pofs, int transpose,
+                   cudaStream_t s);
+
+// Final FP64 accumulation: U[perm[m]] = alpha1 F_m + y_near(m) + the block
+// partials of every admissible block containing m (rowG / order index the
+// blocks by the accumulated side: targets, or sources when transposed).
+void accumulate_impl(hh_ctx* ctx, const hh_tree* t, const hh_params& p, const double* Fs, const void* y_near,
+                     const void* part, const int64_t* pofs, const int64_t* rowG, const int32_t* order, double alpha1,
+                     double* U, cudaStream_t s);
+
+// Partial-output offsets: pofs[b] = sum_{b' < b} |target(b')| (or source if
+// transpose); returns the total (synchronises).
+int64_t partial_offsets(const hh_tree* t, const hh_blocks* b, int transpose, int64_t* pofs, cudaStream_t s);
+
+// Parameters a kernel of real type R copies to shared memory.
+template <typename R>
+inline const R* theta_for(const hh_ctx* ctx, const hh_params& p, int* n)
+{
+    if (p.kernel == HH_RPY) { *n = 0; return nullptr; }
+    if constexpr (sizeof(R) == 8) { *n = ctx->n_theta; return (const R*)ctx->theta64; }
+    else { *n = ctx->n_theta_t; return (const R*)ctx->theta32t; }
+}
+
+inline int real_bytes(const hh_params& p) { return p.precision == HH_FP64 ? 8 : 4; }
+inline int kernel_kind(const hh_params& p, int width) { return p.kernel == HH_RPY ? 2 : (width == 64 ? 1 : 0); }

@@ -1,0 +1,249 @@
+// hh_near.cu -- inadmissible (dense) blocks, partial offsets and the final
+// FP64 accumulation of U (Section 3.3, "Inadmissible blocks"; Eq. 6).
+//
+// Near field: one warp per target leaf tau walks every inadmissible block
+// (tau, sigma) of its row.  Lane l serves target row (l mod c') and source
+// subset (l div c'), c' = next power of two >= |tau| (<= 32), so leaves
+// smaller than a warp still keep all lanes busy; the subsets are folded with
+// xor-shuffles in a fixed order, so the result is bit-reproducible.  The self
+// pair (m == n) is skipped: it is the single-body term alpha_1.
+//
+// Accumulation: for every particle m (sorted order) the FP64 sum
+//   U_m = alpha_1 F_m + y_near(m) + sum over the ancestors tau of m, and the
+//         admissible blocks (tau, sigma) of each, of the block partial at m,
+// taken root to leaf, sources ascending; written to the caller's row perm[m].
+#include <algorithm>
+
+#include "hh_internal.h"
+
+namespace {
+
+constexpr int NEAR_WPB = 4;
+
+template <typename R, int KIND>
+__global__ void __launch_bounds__(32 * NEAR_WPB) k_near(const double* __restrict__ Xs, const double* __restrict__ Fs,
+                                                        const int32_t* __restrict__ PH, const int64_t* __restrict__ rowH,
+                                                        const int32_t* __restrict__ work, int64_t n_work,
+                                                        const int32_t* __restrict__ nbeg,
+                                                        const int32_t* __restrict__ nend, const R* __restrict__ th_g,
+                                                        int n_th, PairParams pp, int transpose, R* __restrict__ y,
+                                                        unsigned long long* n_pairs)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* th = reinterpret_cast<R*>(smem_raw);
+    for (int i = threadIdx.x; i < n_th; i += blockDim.x) th[i] = th_g[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (int64_t)blockIdx.x * NEAR_WPB + (threadIdx.x >> 5);
+    const int64_t nwarps = (int64_t)gridDim.x * NEAR_WPB;
+    for (int64_t w = wid; w < n_work; w += nwarps) {
+        const int32_t tau = work[w];
+        const int32_t t0 = nbeg[tau], c = nend[tau] - t0;
+        int cp = 1;
+        while (cp < c && cp < 32) cp <<= 1;
+        const int G = 32 / cp;            // source subsets
+        const int row = lane % cp, g = lane / cp;
+        const int rpl = (c + 31) / 32;    // rows per lane when c > 32 (then G == 1)
+        R acc[4][3];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = acc[i][2] = 0;
+        int64_t pairs = 0;
+        for (int64_t bb = rowH[tau]; bb < rowH[tau + 1]; ++bb) {
+            const int32_t sg = PH[2 * bb + 1];
+            const int32_t s0 = nbeg[sg], q = nend[sg] - s0;
+            for (int n = g; n < q; n += G) {
+                const int64_t gn = s0 + n;
+                const double* f = Fs + 3 * gn;
+                const R f0 = (R)f[0], f1 = (R)f[1], f2 = (R)f[2];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (i >= rpl) break;
+                    const int m = row + 32 * i;
+                    if (m >= c) break;
+                    const int64_t gm = t0 + m;
+                    if (gm == gn) continue;
+                    R rx, ry, rz, K[9];
+                    if (!transpose) sep<R>(Xs, gm, gn, rx, ry, rz);
+                    else sep<R>(Xs, gn, gm, rx, ry, rz);
+                    pair_block<R, KIND>(th, pp, rx, ry, rz, K);
+                    acc[i][0] += K[0] * f0 + K[1] * f1 + K[2] * f2;
+                    acc[i][1] += K[3] * f0 + K[4] * f1 + K[5] * f2;
+                    acc[i][2] += K[6] * f0 + K[7] * f1 + K[8] * f2;
+                    ++pairs;
+                }
+            }
+        }
+        for (int o = cp; o < 32; o <<= 1)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) acc[i][a] += __shfl_xor_sync(0xffffffffu, acc[i][a], o);
+        if (g == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (i >= rpl) break;
+                const int m = row + 32 * i;
+                if (m >= c) break;
+                R* out = y + 3 * (int64_t)(t0 + m);
+                out[0] = acc[i][0]; out[1] = acc[i][1]; out[2] = acc[i][2];
+            }
+        }
+        pairs = warp_sum(pairs);
+        if (lane == 0) atomicAdd(n_pairs, (unsigned long long)pairs);
+    }
+}
+
+// Leaves of this shard: flag[t] = 1 for leaf nodes with (t mod shards == shard).
+__global__ void k_leaf_flags(const int32_t* __restrict__ child, int32_t n_nodes, int shard, int n_shards,
+                             int64_t* __restrict__ flag)
+{
+    int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_nodes) flag[t] = child[2 * t] < 0 && (t % n_shards) == shard;
+}
+
+__global__ void k_compact32(const int64_t* __restrict__ flag, const int64_t* __restrict__ off, int64_t n,
+                            int32_t* __restrict__ out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && flag[i]) out[off[i]] = (int32_t)i;
+}
+
+template <typename R, int KIND>
+void launch_near(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_params& p, const double* Fs, R* y,
+                 const int32_t* work, int64_t n_work, int transpose, cudaStream_t s)
+{
+    int n_th = 0;
+    const R* th = theta_for<R>(ctx, p, &n_th);
+    const size_t smem = sizeof(R) * (size_t)n_th;
+    HH_CUDA(cudaFuncSetAttribute(k_near<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t blocks = std::min<int64_t>(ceil_div(n_work, NEAR_WPB), (int64_t)ctx->n_sm * 16);
+    k_near<R, KIND><<<(unsigned)blocks, 32 * NEAR_WPB, smem, s>>>(
+        t->Xs, Fs, b->PH, b->rowH, work, n_work, t->nbeg, t->nend, th, n_th, PairParams{p.radius, p.viscosity},
+        transpose, y, ctx->d_counters + 5);
+    HH_CHECK_LAUNCH();
+}
+
+template <typename R>
+__global__ void k_accum(int64_t n, const double* __restrict__ Fs, const R* __restrict__ ynear,
+                        const R* __restrict__ part, const int64_t* __restrict__ pofs, const int64_t* __restrict__ rowG,
+                        const int32_t* __restrict__ order, const int32_t* __restrict__ child,
+                        const int32_t* __restrict__ nbeg, const int32_t* __restrict__ nend,
+                        const int64_t* __restrict__ off, int B, const int32_t* __restrict__ perm, double a1,
+                        double* __restrict__ U)
+{
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= m) lo = mid; else hi = mid - 1;
+    }
+    double u0 = a1 * Fs[3 * m], u1 = a1 * Fs[3 * m + 1], u2 = a1 * Fs[3 * m + 2];
+    if (ynear) {
+        u0 += (double)ynear[3 * m];
+        u1 += (double)ynear[3 * m + 1];
+        u2 += (double)ynear[3 * m + 2];
+    }
+    int32_t node = lo;
+    if (part) {
+        for (;;) {
+            const int64_t r0 = rowG[node], r1 = rowG[node + 1];
+            const int64_t loc = m - nbeg[node];
+            for (int64_t k = r0; k < r1; ++k) {
+                const int64_t blk = order ? order[k] : k;
+                const R* pb = part + 3 * (pofs[blk] + loc);
+                u0 += (double)pb[0];
+                u1 += (double)pb[1];
+                u2 += (double)pb[2];
+            }
+            const int32_t c0 = child[2 * node];
+            if (c0 < 0) break;
+            node = m < nend[c0] ? c0 : child[2 * node + 1];
+        }
+    }
+    const int64_t dst = perm[m];
+    U[3 * dst] = u0;
+    U[3 * dst + 1] = u1;
+    U[3 * dst + 2] = u2;
+}
+
+__global__ void k_block_len(const int32_t* __restrict__ PG, int64_t nG, const int32_t* __restrict__ nbeg,
+                            const int32_t* __restrict__ nend, int side, int64_t* __restrict__ len)
+{
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nG) {
+        int32_t nd = PG[2 * b + side];
+        len[b] = nend[nd] - nbeg[nd];
+    }
+}
+
+}  // namespace
+
+void near_field(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_params& p, const double* Fs, void* y,
+                int transpose, cudaStream_t s)
+{
+    HH_REQUIRE(p.leaf_size <= 129, HH_ERR_ARG, "leaf_size must be <= 129 (a near-field warp holds <= 128 rows)");
+    const int32_t nn = t->n_nodes;
+    int64_t* flag = dev_alloc_t<int64_t>(nn, s);
+    int64_t* off = dev_alloc_t<int64_t>(nn, s);
+    int64_t* tot = dev_alloc_t<int64_t>(1, s);
+    k_leaf_flags<<<(unsigned)ceil_div(nn, 256), 256, 0, s>>>(t->child, nn, p.shard_id, p.n_shards, flag);
+    HH_CHECK_LAUNCH();
+    dev_scan_i64(flag, off, nn, tot, s);
+    int64_t n_work = 0;
+    HH_CUDA(cudaMemcpyAsync(&n_work, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HH_CUDA(cudaStreamSynchronize(s));
+    int32_t* work = dev_alloc_t<int32_t>(n_work, s);
+    k_compact32<<<(unsigned)ceil_div(nn, 256), 256, 0, s>>>(flag, off, nn, work);
+    HH_CHECK_LAUNCH();
+    HH_CUDA(cudaMemsetAsync(y, 0, (size_t)real_bytes(p) * 3 * t->n, s));
+    if (n_work > 0) {
+        const int kind = kernel_kind(p, ctx->width);
+        if (p.precision == HH_FP64) {
+            if (kind == 0) launch_near<double, 0>(ctx, t, b, p, Fs, (double*)y, work, n_work, transpose, s);
+            else if (kind == 1) launch_near<double, 1>(ctx, t, b, p, Fs, (double*)y, work, n_work, transpose, s);
+            else launch_near<double, 2>(ctx, t, b, p, Fs, (double*)y, work, n_work, transpose, s);
+        } else {
+            if (kind == 0) launch_near<float, 0>(ctx, t, b, p, Fs, (float*)y, work, n_work, transpose, s);
+            else if (kind == 1) launch_near<float, 1>(ctx, t, b, p, Fs, (float*)y, work, n_work, transpose, s);
+            else launch_near<float, 2>(ctx, t, b, p, Fs, (float*)y, work, n_work, transpose, s);
+        }
+    }
+    dev_free(flag, s);
+    dev_free(off, s);
+    dev_free(tot, s);
+    dev_free(work, s);
+}
+
+int64_t partial_offsets(const hh_tree* t, const hh_blocks* b, int transpose, int64_t* pofs, cudaStream_t s)
+{
+    const int64_t nG = b->nG;
+    if (nG == 0) return 0;
+    int64_t* len = dev_alloc_t<int64_t>(nG, s);
+    int64_t* tot = dev_alloc_t<int64_t>(1, s);
+    k_block_len<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(b->PG, nG, t->nbeg, t->nend, transpose ? 1 : 0, len);
+    HH_CHECK_LAUNCH();
+    dev_scan_i64(len, pofs, nG, tot, s);
+    int64_t h = 0;
+    HH_CUDA(cudaMemcpyAsync(&h, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HH_CUDA(cudaStreamSynchronize(s));
+    dev_free(len, s);
+    dev_free(tot, s);
+    return h;
+}
+
+void accumulate_impl(hh_ctx* ctx, const hh_tree* t, const hh_params& p, const double* Fs, const void* y_near,
+                     const void* part, const int64_t* pofs, const int64_t* rowG, const int32_t* order, double alpha1,
+                     double* U, cudaStream_t s)
+{
+    (void)ctx;
+    const int64_t n = t->n;
+    const unsigned grid = (unsigned)ceil_div(n, 256);
+    if (real_bytes(p) == 8)
+        k_accum<double><<<grid, 256, 0, s>>>(n, Fs, (const double*)y_near, (const double*)part, pofs, rowG, order,
+                                             t->child, t->nbeg, t->nend, t->d_offsets, t->batch, t->perm, alpha1, U);
+    else
+        k_accum<float><<<grid, 256, 0, s>>>(n, Fs, (const float*)y_near, (const float*)part, pofs, rowG, order,
+                                            t->child, t->nbeg, t->nend, t->d_offsets, t->batch, t->perm, alpha1, U);
+    HH_CHECK_LAUNCH();
+}

@@ -1,0 +1,243 @@
+"""Parity of the CUDA path (through the C-ABI) against the FP64 CPU oracle.
+
+Integer/index results (Morton codes, permutation, tree, block lists) must be
+bit-identical.  Velocities: FP64 mode against the oracle's H-matrix product to
+1e-11 relative (same algorithm, different summation order); FP32 mode to
+2e-5 relative of the oracle's H-matrix product (FP32 rounding of ~10^3-term
+sums, observed ~1e-6) and to eps_r <= zeta against the exact dense product
+(Eq. 11, the paper's own bound).
+"""
+import numpy as np
+import pytest
+
+import hh_synth
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2505_08174_b300 as hh  # noqa: E402
+
+THETA32 = hh_synth.mlp_params(32, 7)
+THETA64 = hh_synth.mlp_params(64, 7)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = hh.Context()
+    c.set_mlp(THETA32, 32)
+    return c
+
+
+def cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def kern(kind="mlp", width=32):
+    return oracle.PairKernel(kind, THETA32 if width == 32 else THETA64, width)
+
+
+# --------------------------------------------------------------------------
+# tree and partition: bit-exact
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,leaf", [(1, 32), (2, 2), (31, 32), (32, 32), (33, 32), (1024, 32), (5000, 16),
+                                    (3000, 64)])
+def test_tree_bit_exact(ctx, n, leaf):
+    X = hh_synth.rsa_cube(n, 0.1, seed=n) if n > 1 else np.array([[1.0, 2.0, 3.0]])
+    t = ctx.build_tree(cuda(X), hh.Params(leaf_size=leaf))
+    g = t.export()
+    o = oracle.build_tree(X, leaf)
+    assert np.array_equal(g["perm"], o.perm)
+    assert np.array_equal(g["codes"], o.codes)
+    assert np.array_equal(g["begin"], o.begin) and np.array_equal(g["end"], o.end)
+    assert np.array_equal(g["child"], o.child)
+    assert np.array_equal(g["lo"], o.lo) and np.array_equal(g["hi"], o.hi)
+
+
+def test_tree_duplicate_codes_and_degenerate_extent(ctx):
+    # 40 points on 2 sites (equal codes force the begin + size/2 split) and a flat plane
+    X = np.zeros((40, 3)); X[20:, 0] = 1.0
+    Y = np.random.default_rng(0).uniform(0, 10, size=(200, 3)); Y[:, 2] = 5.0
+    for A in (X, Y):
+        g = ctx.build_tree(cuda(A), hh.Params(leaf_size=8)).export()
+        o = oracle.build_tree(A, 8)
+        assert np.array_equal(g["perm"], o.perm) and np.array_equal(g["begin"], o.begin)
+        assert np.array_equal(g["child"], o.child) and np.array_equal(g["lo"], o.lo)
+
+
+@pytest.mark.parametrize("eta", [0.7, 1.0, 1.5])
+def test_partition_bit_exact(ctx, eta):
+    X = hh_synth.rsa_cube(4096, 0.1, seed=3)
+    p = hh.Params(leaf_size=32, eta=eta)
+    t = ctx.build_tree(cuda(X), p)
+    G, H = ctx.partition(t, p).export()
+    ot = oracle.build_tree(X, 32)
+    oG, oH = oracle.partition(ot, 32, eta)
+    assert np.array_equal(G, oG) and np.array_equal(H, oH)
+
+
+def test_batch_tree_matches_instances(ctx):
+    sizes = [700, 1, 1500, 64]
+    Xs = [hh_synth.rsa_cube(s, 0.1, seed=10 + i) if s > 1 else np.array([[0.5, 0.5, 0.5]])
+          for i, s in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    g = ctx.build_tree(cuda(np.concatenate(Xs)), hh.Params(leaf_size=32), offsets=off).export()
+    for b, X in enumerate(Xs):
+        o = oracle.build_tree(X, 32)
+        assert np.array_equal(g["perm"][off[b]:off[b + 1]] - off[b], o.perm)
+        assert np.array_equal(g["codes"][off[b]:off[b + 1]], o.codes)
+        # node ranges of this instance (the forest interleaves instances level by level)
+        mine = (g["begin"] >= off[b]) & (g["end"] <= off[b + 1])
+        rng_g = sorted(zip((g["begin"][mine] - off[b]).tolist(), (g["end"][mine] - off[b]).tolist()))
+        assert rng_g == sorted(zip(o.begin.tolist(), o.end.tolist()))
+
+
+# --------------------------------------------------------------------------
+# ACA pivots and ranks (FP64 mode)
+# --------------------------------------------------------------------------
+def test_aca_fp64_ranks_and_pivots(ctx):
+    X = hh_synth.rsa_cube(2048, 0.1, seed=5)
+    F = hh_synth.forces(2048, 0)
+    p = hh.Params(precision="fp64", eps=1e-4, max_rank=48)
+    t = ctx.build_tree(cuda(X), p)
+    b = ctx.partition(t, p)
+    h = ctx.aca(t, b, p)
+    ranks, pI, pJ = h.export()
+    _, st = oracle.hmatvec(X, F, kern(), leaf=32, eta=1.0, eps=1e-4, max_rank=48, want_ranks=True)
+    same = (ranks == st["ranks"]) & np.all(pI == st["pivI"], axis=1) & np.all(pJ == st["pivJ"], axis=1)
+    # rounding-level differences in the MLP may flip a near-tie; allow at most 0.5% of blocks
+    assert same.mean() >= 0.995, f"{(~same).sum()} of {len(same)} blocks differ"
+    assert ranks.sum() == pytest.approx(st["ranks"].sum(), rel=2e-3)
+
+
+# --------------------------------------------------------------------------
+# velocities
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["mlp", "rpy"])
+def test_predict_fp64_matches_oracle_hmatvec(ctx, kind):
+    n = 2048
+    X = hh_synth.rsa_cube(n, 0.1, seed=6)
+    F = hh_synth.forces(n, 1)
+    U = ctx.predict(cuda(X), cuda(F), hh.Params(precision="fp64", kernel=kind)).cpu().numpy()
+    Uo, _ = oracle.hmatvec(X, F, kern(kind), leaf=32, eta=1.0, eps=1e-4, max_rank=48)
+    assert oracle.rel_error(Uo, U) < 1e-11
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4, 1e-6])
+def test_predict_fp32_against_dense(ctx, eps):
+    n = 1024
+    X = hh_synth.rsa_cube(n, 0.1)
+    ks = kern()
+    errs = []
+    for s in range(5):   # Eq. 11 averaged over 5 force vectors
+        F = hh_synth.forces(n, s)
+        U = ctx.predict(cuda(X), cuda(F), hh.Params(precision="fp32", eps=eps)).cpu().numpy()
+        Ud = oracle.dense_matvec(X, F, ks, with_self=True)
+        a1 = oracle.self_mobility()
+        errs.append(oracle.rel_error(Ud - a1 * F, U - a1 * F))
+        if s == 0:
+            Uo, _ = oracle.hmatvec(X, F, ks, leaf=32, eta=1.0, eps=eps, max_rank=48)
+            assert oracle.rel_error(Uo, U) < 2e-5
+    assert np.mean(errs) <= eps
+
+
+def test_predict_ragged_and_tiny(ctx):
+    a1 = oracle.self_mobility()
+    for n in (1, 2, 3, 37, 257):
+        X = hh_synth.rsa_cube(n, 0.1, seed=n) if n > 1 else np.array([[3.0, 1.0, 2.0]])
+        F = hh_synth.forces(n, n)
+        U = ctx.predict(cuda(X), cuda(F), hh.Params(precision="fp64")).cpu().numpy()
+        Ud = oracle.dense_matvec(X, F, kern())
+        assert oracle.rel_error(Ud, U) < 1e-12 if n < 64 else oracle.rel_error(Ud, U) < 1e-4
+        if n == 1:
+            assert np.allclose(U, a1 * F, rtol=1e-15)
+
+
+def test_predict_width64(ctx):
+    c = hh.Context()
+    c.set_mlp(THETA64, 64)
+    n = 1500
+    X = hh_synth.rsa_cube(n, 0.1, seed=8)
+    F = hh_synth.forces(n, 2)
+    Uo, _ = oracle.hmatvec(X, F, kern("mlp", 64), leaf=64, eta=1.0, eps=1e-4, max_rank=48)
+    for prec, tol in (("fp64", 1e-11), ("fp32", 2e-5)):
+        U = c.predict(cuda(X), cuda(F), hh.Params(precision=prec, leaf_size=64)).cpu().numpy()
+        assert oracle.rel_error(Uo, U) < tol
+
+
+def test_staged_matvec_equals_predict_and_transpose_is_adjoint(ctx):
+    n = 2048
+    X = hh_synth.rsa_cube(n, 0.1, seed=9)
+    F = hh_synth.forces(n, 3)
+    W = hh_synth.forces(n, 4)
+    p = hh.Params(precision="fp64")
+    Xd = cuda(X)
+    t = ctx.build_tree(Xd, p)
+    b = ctx.partition(t, p)
+    h = ctx.aca(t, b, p)
+    U1 = ctx.matvec(h, cuda(F)).cpu().numpy()
+    U2 = ctx.predict(Xd, cuda(F), p).cpu().numpy()
+    assert oracle.rel_error(U2, U1) < 1e-13
+    UT = ctx.matvec(h, cuda(W), transpose=True).cpu().numpy()
+    lhs = np.sum(W * U1)
+    rhs = np.sum(UT * F)
+    assert abs(lhs - rhs) <= 1e-12 * np.sqrt(np.sum(W * W) * np.sum(U1 * U1))
+
+
+def test_shards_sum_to_whole(ctx):
+    n = 3000
+    X = hh_synth.rsa_cube(n, 0.1, seed=11)
+    F = hh_synth.forces(n, 5)
+    Xd, Fd = cuda(X), cuda(F)
+    full = ctx.predict(Xd, Fd, hh.Params(precision="fp64")).cpu().numpy()
+    parts = [ctx.predict(Xd, Fd, hh.Params(precision="fp64", shard_id=s, n_shards=3)).cpu().numpy()
+             for s in range(3)]
+    assert oracle.rel_error(full, sum(parts)) < 1e-14
+
+
+def test_batch_predict_equals_separate(ctx):
+    sizes = [900, 1300, 2]
+    Xs = [hh_synth.rsa_cube(s, 0.1, seed=20 + i) for i, s in enumerate(sizes)]
+    Fs = [hh_synth.forces(s, 30 + i) for i, s in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    p = hh.Params(precision="fp64")
+    Ub = ctx.predict(cuda(np.concatenate(Xs)), cuda(np.concatenate(Fs)), p, offsets=off).cpu().numpy()
+    for i in range(len(sizes)):
+        Ui = ctx.predict(cuda(Xs[i]), cuda(Fs[i]), p).cpu().numpy()
+        assert np.array_equal(Ub[off[i]:off[i + 1]], Ui)
+
+
+def test_deterministic(ctx):
+    n = 4000
+    X, F = cuda(hh_synth.rsa_cube(n, 0.1, seed=12)), cuda(hh_synth.forces(n, 6))
+    p = hh.Params(precision="fp32")
+    a = ctx.predict(X, F, p).cpu().numpy()
+    b = ctx.predict(X, F, p).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_larger_sampled_rows(ctx):
+    n = 30000
+    X = hh_synth.rsa_cube(n, 0.1, seed=13)
+    F = hh_synth.forces(n, 7)
+    U = ctx.predict(cuda(X), cuda(F), hh.Params(precision="fp32", eps=1e-4)).cpu().numpy()
+    rows = np.arange(0, n, 97)
+    Ud = oracle.dense_matvec(X, F, kern(), rows=rows, with_self=False)
+    a1 = oracle.self_mobility()
+    assert oracle.rel_error(Ud, U[rows] - a1 * F[rows]) <= 1e-4
+    st = ctx.stats()
+    assert st["n_blocks_G"] > 0 and st["n_aca_queries"] > 0 and st["n_near_pairs"] > 0
+
+
+def test_bad_arguments(ctx):
+    X = cuda(hh_synth.rsa_cube(100, 0.1))
+    with pytest.raises(hh.HHError) as e:
+        ctx.predict(X, X, hh.Params(max_rank=65))
+    assert e.value.status == hh.HH_ERR_ARG
+    with pytest.raises(hh.HHError):
+        ctx.predict(X, X, hh.Params(leaf_size=1))
+    bad = X.clone()
+    bad[5, 1] = float("nan")
+    with pytest.raises(hh.HHError) as e:
+        ctx.predict(bad, X, hh.Params())
+    assert e.value.status == hh.HH_ERR_NUMERIC
