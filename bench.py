@@ -1,0 +1,279 @@
+"""Benchmark: particle-velocities/s of one H-HIGNN prediction U = M(X) F.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--n 1000000] [--impl ours|reference]
+
+A step is one full prediction through the C-ABI (hh_predict): Morton tree,
+admissibility partition, batched ACA fused with the low-rank apply, dense
+inadmissible blocks, FP64 accumulation.  Workload: N = 1,000,000 spheres
+(a = 1) placed by random sequential addition in a cube at volume fraction
+0.1, forces N(0,1), pair MLP 4->32->32->32->6 (SiLU, Xavier weights rounded to
+bf16), C_leaf = 32, eta = 1, zeta = 1e-4, max_rank 48, FP32 kernels with FP64
+pivots / norms / accumulation.
+
+value    = N * K / (sum of CUDA-event times of the K predictions), inputs
+           resident in HBM; L2 (126 MB) is flushed between steps by writing a
+           256 MB buffer (outside the event pairs).
+e2e      = same metric through the same call with the inputs in pinned host
+           memory: H2D copy of X and F, prediction, D2H copy of U, per step.
+rel_err  = Eq. 11 (M^(t,2) part only) against the FP64 dense oracle on 64
+           sampled target rows.
+roofline = the ACA team kernels (the dominant stage): algorithmic FP32 flop
+           (5145 per pair-kernel query of the width-32 MLP) / their event time,
+           against the FP32 FMA peak of 148 SMs x 128 lanes x 2 flop x
+           2.032 GHz = 77.0 TFLOP/s ("alu" bound).
+cpu_baseline = the FP64 CPU oracle as it stands: 64 sampled rows of the exact
+           dense product on the host cores, scaled to particle-velocities/s.
+
+Under torchrun each rank runs its own independent suspension of N particles
+(weak scaling, no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOP_PER_QUERY = {32: 2 * (4 * 32 + 32 * 32 + 32 * 32 + 32 * 6) + 4 * 96 + 25,
+                  64: 2 * (4 * 64 + 64 * 64 + 64 * 64 + 64 * 6) + 4 * 192 + 25}
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+METRIC = "particle-velocities/sec per H-HIGNN prediction at N=1M; rel. L2 err vs FP64 dense"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [l.split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in rows if len(r) >= 9]
+        mx = [float(r[2]) for r in rows if len(r) >= 9]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4)
+                          if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def workload(n, seed_geom=1234):
+    import hh_synth
+    X = hh_synth.rsa_cube(n, 0.1, seed=seed_geom)
+    F = hh_synth.forces(n, 0)
+    theta = hh_synth.mlp_params(32, 7)
+    return X, F, theta
+
+
+def cpu_baseline(X, F, theta, rows=64, seed=0):
+    """The oracle as it stands: exact dense FP64 rows on the host cores."""
+    import oracle
+    k = oracle.PairKernel("mlp", theta, 32)
+    idx = np.sort(np.random.default_rng(seed).choice(len(X), rows, replace=False))
+    t0 = time.perf_counter()
+    Ud = oracle.dense_matvec(X, F, k, rows=idx, with_self=False)
+    dt = time.perf_counter() - t0
+    return idx, Ud, rows / dt, oracle.num_threads(), dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    X, F, theta = workload(args.n)
+    for _ in range(args.warmup):
+        cpu_baseline(X, F, theta, rows=8, seed=99)
+    tot_rows, tot_t = 0, 0.0
+    for s in range(args.steps):
+        _, _, rate, cores, dt = cpu_baseline(X, F, theta, rows=args.ref_rows, seed=s)
+        tot_rows += args.ref_rows
+        tot_t += dt
+    v = tot_rows / tot_t
+    sample = f"{args.ref_rows} sampled target rows of the N={args.n} exact dense FP64 product per step"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "particle-velocities/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"uniform_cube_rsa_N{args.n}_phi0.1_mlp4-32-32-32-6", "n": args.n},
+            "cpu_baseline": {"value": v, "unit": "particle-velocities/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "particle-velocities/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2505_08174_b300 as hh
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    X, F, theta = workload(args.n, seed_geom=1234 + rank)
+    n = len(X)
+    ctx = hh.Context(dev)
+    ctx.set_mlp(theta, 32)
+    prec = args.precision
+    p = hh.Params(leaf_size=32, eta=1.0, eps=args.eps, max_rank=48, precision=prec)
+    Xd = torch.as_tensor(X).cuda()
+    Fd = torch.as_tensor(F).cuda()
+    U = torch.empty_like(Xd)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        ctx.predict(Xd, Fd, p, out=U)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_aca_kern, queries, launches = 0.0, 0, 0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        for s in range(args.steps):
+            flush.fill_(float(s))
+            ev[s][0].record(stream)
+            ctx.predict(Xd, Fd, p, out=U)
+            ev[s][1].record(stream)
+            st = ctx.stats()
+            t_aca_kern += st.get("t_kernel_aca", st["t_aca"])
+            queries += st["n_aca_queries"]
+            launches += st.get("n_launches", 0)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(np.sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = n * world * args.steps / (total_ms / 1e3)
+    clocks = clk.summary()
+    st = ctx.stats()
+
+    # end to end: pinned host inputs, H2D + predict + D2H per step
+    Xh = torch.as_tensor(X).pin_memory()
+    Fh = torch.as_tensor(F).pin_memory()
+    Uh = torch.empty_like(Xh).pin_memory()
+    e2e_t = []
+    for s in range(max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Xd.copy_(Xh, non_blocking=True)
+        Fd.copy_(Fh, non_blocking=True)
+        ctx.predict(Xd, Fd, p, out=U)
+        Uh.copy_(U, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_value = n * world / float(np.mean(e2e_t))
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # accuracy (Eq. 11 on M^(t,2) F) and the CPU baseline from the same sampled rows
+    import oracle
+    a1 = oracle.self_mobility()
+    idx, Ud, cpu_rate, cores, cpu_dt = cpu_baseline(X, F, theta, rows=args.ref_rows)
+    Ug = Uh.numpy()[idx] - a1 * F[idx]
+    rel_err = float(oracle.rel_error(Ud, Ug))
+
+    peaks = _peaks()
+    flops = queries / args.steps * FLOP_PER_QUERY[32]
+    aca_ms = t_aca_kern / args.steps
+    achieved = flops / (aca_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "particle-velocities/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else prec, "data": "synthetic",
+        "config": {"workload": f"uniform_cube_rsa_N{n}_phi0.1_mlp4-32-32-32-6", "n": n, "leaf_size": 32,
+                   "eta": 1.0, "eps": args.eps, "max_rank": 48, "precision": prec,
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"independent suspension per GPU"},
+        "rel_err": rel_err, "rel_err_rows": len(idx),
+        "stages_ms": {k: st[k] for k in ("t_tree", "t_part", "t_near", "t_aca", "t_acc")},
+        "counts": {"n_aca_queries": st["n_aca_queries"], "n_near_pairs": st["n_near_pairs"],
+                   "n_blocks_G": st["n_blocks_G"], "n_blocks_H": st["n_blocks_H"], "n_nodes": st["n_nodes"]},
+        "roofline": {"bound": "alu", "kernel": "k_aca_cta + k_aca_warp (block ACA teams)",
+                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz (no measured FP32 peak)"},
+        "cpu_baseline": {"value": cpu_rate, "unit": "particle-velocities/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{len(idx)} target rows of the N={n} exact dense FP64 product ({cpu_dt:.1f} s)"},
+        "e2e": {"value": e2e_value, "unit": "particle-velocities/s", "h2d_bytes_per_step": 2 * 24 * n,
+                "d2h_bytes_per_step": 24 * n},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz")},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-rows", type=int, default=64)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

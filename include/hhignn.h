@@ -172,6 +172,9 @@ typedef struct {
     int64_t n_aca_queries;  /* pair-kernel evaluations inside ACA            */
     int64_t n_blocks_G, n_blocks_H, n_nodes;
     int64_t rank_hist[65];  /* rank_hist[min(rank, 64)] (hh_aca only)        */
+    double t_kernel_aca;    /* ms inside the ACA team kernels (CUDA events)   */
+    double t_kernel_near;   /* ms inside the near-field kernel (CUDA events)  */
+    int64_t n_launches;     /* kernels this library launched in the call      */
 } hh_stats_t;
 
 /* Counters of the last hh_predict / hh_aca on ctx. */

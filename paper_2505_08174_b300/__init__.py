@@ -55,7 +55,8 @@ class CStats(ctypes.Structure):
                 ("t_aca", ctypes.c_double), ("t_apply", ctypes.c_double), ("t_acc", ctypes.c_double),
                 ("n_near_pairs", ctypes.c_int64), ("n_aca_queries", ctypes.c_int64),
                 ("n_blocks_G", ctypes.c_int64), ("n_blocks_H", ctypes.c_int64), ("n_nodes", ctypes.c_int64),
-                ("rank_hist", ctypes.c_int64 * 65)]
+                ("rank_hist", ctypes.c_int64 * 65), ("t_kernel_aca", ctypes.c_double),
+                ("t_kernel_near", ctypes.c_double), ("n_launches", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p

@@ -552,8 +552,11 @@ void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_
         B.team_stride = stride;
         size_t smem = sizeof(TeamSmem<R>) + th_bytes;
         HH_CUDA(cudaFuncSetAttribute(k_aca_cta<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HH_CUDA(cudaEventRecord(ctx->kev[0], s));
         k_aca_cta<R, KIND><<<(unsigned)teams, CTA_T, smem, s>>>(B, mode);
         HH_CHECK_LAUNCH();
+        HH_CUDA(cudaEventRecord(ctx->kev[1], s));
+        ctx->kev_aca_used |= 1;
         dev_free(scratch, s);
     }
     if (n_small > 0) {
@@ -570,8 +573,11 @@ void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_
         B.team_stride = stride;
         size_t smem = WPB * sizeof(TeamSmem<R>) + th_bytes;
         HH_CUDA(cudaFuncSetAttribute(k_aca_warp<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HH_CUDA(cudaEventRecord(ctx->kev[2], s));
         k_aca_warp<R, KIND><<<(unsigned)blocks, 32 * WPB, smem, s>>>(B, mode);
         HH_CHECK_LAUNCH();
+        HH_CUDA(cudaEventRecord(ctx->kev[3], s));
+        ctx->kev_aca_used |= 2;
         dev_free(scratch, s);
     }
 }

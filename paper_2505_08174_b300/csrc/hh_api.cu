@@ -81,6 +81,25 @@ void reset_call(hh_ctx* ctx, cudaStream_t s)
     HH_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s));
     HH_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 8 * sizeof(unsigned long long), s));
     ctx->last_stream = s;
+    ctx->kev_aca_used = 0;
+    ctx->kev_near_used = 0;
+    ctx->launch_base = g_hh_launches;
+}
+
+// Kernel event times and the launch count of the call (after a stream sync).
+void finish_stats(hh_ctx* ctx)
+{
+    float ms = 0.f;
+    double aca = 0.0;
+    if (ctx->kev_aca_used & 1) { HH_CUDA(cudaEventElapsedTime(&ms, ctx->kev[0], ctx->kev[1])); aca += ms; }
+    if (ctx->kev_aca_used & 2) { HH_CUDA(cudaEventElapsedTime(&ms, ctx->kev[2], ctx->kev[3])); aca += ms; }
+    ctx->stats.t_kernel_aca = aca;
+    ctx->stats.t_kernel_near = 0.0;
+    if (ctx->kev_near_used) {
+        HH_CUDA(cudaEventElapsedTime(&ms, ctx->kev[4], ctx->kev[5]));
+        ctx->stats.t_kernel_near = ms;
+    }
+    ctx->stats.n_launches = (int64_t)(g_hh_launches - ctx->launch_base);
 }
 
 hh_status read_status(hh_ctx* ctx, cudaStream_t s)
@@ -163,6 +182,7 @@ hh_status hh_create(hh_ctx** out, int device)
         HH_CUDA(cudaMemset(ctx->d_status, 0, sizeof(unsigned)));
         HH_CUDA(cudaMemset(ctx->d_counters, 0, 8 * sizeof(unsigned long long)));
         for (auto& e : ctx->ev) HH_CUDA(cudaEventCreate(&e));
+        for (auto& e : ctx->kev) HH_CUDA(cudaEventCreate(&e));
         return HH_OK;
     });
     cudaSetDevice(prev);
@@ -184,6 +204,8 @@ void hh_destroy(hh_ctx* ctx)
     cudaFree(ctx->d_status);
     cudaFree(ctx->d_counters);
     for (auto& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    for (auto& e : ctx->kev)
         if (e) cudaEventDestroy(e);
     delete ctx;
 }
@@ -327,6 +349,7 @@ hh_status hh_aca(hh_ctx* ctx, const hh_tree* tree, const hh_blocks* blocks, cons
         dev_free(hist, s);
         for (int i = 0; i < 65; ++i) ctx->stats.rank_hist[i] = (int64_t)hh[i];
         ctx->stats.n_aca_queries = (int64_t)cnt[4] / 2;  // the rank loop ran twice
+        finish_stats(ctx);
         ctx->stats.n_blocks_G = nG;
         ctx->stats.n_blocks_H = blocks->nH;
         *out = h;
@@ -434,6 +457,7 @@ hh_status hh_predict(hh_ctx* ctx, const double* X_dev, const double* F_dev, cons
         HH_CUDA(cudaMemcpy(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost));
         ctx->stats.n_aca_queries = (int64_t)cnt[4];
         ctx->stats.n_near_pairs = (int64_t)cnt[5];
+        finish_stats(ctx);
         return w;
     });
     free_blocks(b);

@@ -30,7 +30,14 @@ struct HHError {
                           std::string(#call) + ": " + cudaGetErrorString(_e)};                    \
     } while (0)
 
-#define HH_CHECK_LAUNCH() HH_CUDA(cudaGetLastError())
+// Kernels launched by this library (every launch site is followed by
+// HH_CHECK_LAUNCH); read per call into hh_stats_t.n_launches.
+extern unsigned long long g_hh_launches;
+#define HH_CHECK_LAUNCH()       \
+    do {                        \
+        ++g_hh_launches;        \
+        HH_CUDA(cudaGetLastError()); \
+    } while (0)
 
 #define HH_REQUIRE(cond, status, text)                \
     do {                                              \

@@ -24,6 +24,10 @@ struct hh_ctx {
     hh_stats_t stats{};
     cudaStream_t last_stream = nullptr;
     cudaEvent_t ev[8] = {};
+    cudaEvent_t kev[8] = {};             // around the ACA (0..3) and near (4,5) kernels
+    int kev_aca_used = 0;                // ACA kernel event pairs recorded this call
+    int kev_near_used = 0;
+    unsigned long long launch_base = 0;  // g_hh_launches at the start of the call
 };
 
 struct hh_tree {

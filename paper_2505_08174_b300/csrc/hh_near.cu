@@ -117,10 +117,13 @@ void launch_near(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_par
     const size_t smem = sizeof(R) * (size_t)n_th;
     HH_CUDA(cudaFuncSetAttribute(k_near<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t blocks = std::min<int64_t>(ceil_div(n_work, NEAR_WPB), (int64_t)ctx->n_sm * 16);
+    HH_CUDA(cudaEventRecord(ctx->kev[4], s));
     k_near<R, KIND><<<(unsigned)blocks, 32 * NEAR_WPB, smem, s>>>(
         t->Xs, Fs, b->PH, b->rowH, work, n_work, t->nbeg, t->nend, th, n_th, PairParams{p.radius, p.viscosity},
         transpose, y, ctx->d_counters + 5);
     HH_CHECK_LAUNCH();
+    HH_CUDA(cudaEventRecord(ctx->kev[5], s));
+    ctx->kev_near_used = 1;
 }
 
 template <typename R>

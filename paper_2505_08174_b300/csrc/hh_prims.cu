@@ -5,6 +5,8 @@
 
 #include "hh_internal.h"
 
+unsigned long long g_hh_launches = 0;
+
 void* dev_alloc(size_t bytes, cudaStream_t s)
 {
     void* p = nullptr;
