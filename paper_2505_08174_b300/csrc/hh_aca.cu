@@ -22,8 +22,8 @@
 // Pivot guard: a pivot element with det = 0 or 1/(|P|_F |P^-1|_F) < 1e-10
 // is replaced by the unused row of largest |det|; a zero column residual (or
 // no usable pivot) ends the block with the pairs found so far.
-// Gram partial sums are formed in the working precision and reduced, and
-// the norm recurrence is kept, in FP64.
+// The 3x3 Gram sums are formed and reduced in the working precision; nu^2,
+// the cross term and the lambda^2 recurrence are reduced and kept in FP64.
 #include <algorithm>
 
 #include "hh_internal.h"
@@ -69,8 +69,8 @@ template <typename R>
 struct alignas(16) TeamSmem {
     R qj[MAXR * 9];        // Q_p(j_k), p < k
     R ci[MAXR * 9];        // C_p(i_k), p < k
-    double A[(MAXR + 1) * 9];
-    double tr[MAXR + 1];
+    R A[(MAXR + 1) * 9];   // A_pk, p <= k
+    double red[2][8];      // per-warp partials of nu^2 and the cross term
     R Pi[9];
     R tv[MAXR * 3];
     double rv[8];
@@ -171,40 +171,53 @@ __device__ void gram_cols(const Team& tm, TeamSmem<R>& sm, const R* Cs, int c, i
         }
 #pragma unroll
         for (int e = 0; e < 9; ++e) {
-            double s = warp_sum((double)acc[e]);
+            R s = warp_sum(acc[e]);
             if (lane == 0) sm.A[9 * p + e] = s;
         }
     }
 }
 
-// sm.tr[p] = tr(A_pk B_kp) with B_kp = sum_n q_k(n) q_p(n)^T, p = 0..k.
+// nu^2 = tr(A_kk B_kk) and cross = sum_{p<k} tr(A_pk B_kp), B_kp = sum_n q_k(n) q_p(n)^T.
+// tr(A B) is linear in B, so each thread adds
+//   tr(A_pk q_k(n) q_p(n)^T) = <A_pk q_k(n), q_p(n)>_F
+// over its own columns n and only two scalars are reduced across the team.
+// Thread 0 receives the sums (FP64).
 template <typename R, class Team>
-__device__ void gram_rows(const Team& tm, TeamSmem<R>& sm, const R* Qs, int q, int k)
+__device__ void gram_rows(const Team& tm, TeamSmem<R>& sm, const R* Qs, int q, int k, double& nu2, double& cross)
 {
-    const int lane = threadIdx.x & 31;
+    constexpr int SIZE = Team::SIZE;
+    const int tid = tm.tid(), lane = threadIdx.x & 31;
     const R* Qk = Qs + (int64_t)k * 9 * q;
-    for (int p = tm.warp(); p <= k; p += Team::NW) {
-        const R* Qp = Qs + (int64_t)p * 9 * q;
-        R acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int x = lane; x < q; x += 32) {
-            R a[9], b[9];
-            ld9(Qk, q, x, a);
-            ld9(Qp, q, x, b);
+    R snu = 0, scr = 0;
+    for (int n = tid; n < q; n += SIZE) {
+        R qk[9];
+        ld9(Qk, q, n, qk);
+        for (int p = 0; p <= k; ++p) {
+            R qp[9], T[9];
+            if (p == k) {
 #pragma unroll
-            for (int u = 0; u < 3; ++u)
+                for (int e = 0; e < 9; ++e) qp[e] = qk[e];
+            } else {
+                ld9(Qs + (int64_t)p * 9 * q, q, n, qp);
+            }
+            mm3(sm.A + 9 * p, qk, T);
+            R d = 0;
 #pragma unroll
-                for (int v = 0; v < 3; ++v)
-                    acc[3 * u + v] += a[3 * u] * b[3 * v] + a[3 * u + 1] * b[3 * v + 1] + a[3 * u + 2] * b[3 * v + 2];
+            for (int e = 0; e < 9; ++e) d += T[e] * qp[e];
+            if (p == k) snu += d; else scr += d;
         }
-        double trv = 0.0;
-#pragma unroll
-        for (int e = 0; e < 9; ++e) {
-            double s = warp_sum((double)acc[e]);  // B_kp[u][v], e = 3u + v
-            const int u = e / 3, v = e % 3;
-            trv += sm.A[9 * p + 3 * v + u] * s;    // tr(A B) = sum_{u,v} A[v][u] B[u][v]
-        }
-        if (lane == 0) sm.tr[p] = trv;
     }
+    double a = warp_sum((double)snu), b = warp_sum((double)scr);
+    if constexpr (Team::NW > 1) {
+        if (lane == 0) { sm.red[0][tm.warp()] = a; sm.red[1][tm.warp()] = b; }
+        tm.sync();
+        if (tid == 0) {
+            a = 0.0; b = 0.0;
+            for (int w = 0; w < Team::NW; ++w) { a += sm.red[0][w]; b += sm.red[1][w]; }
+        }
+    }
+    nu2 = a;
+    cross = b;
 }
 
 // ---- the per-block ACA -----------------------------------------------------
@@ -361,11 +374,9 @@ __device__ void aca_block(const AcaArgs<R>& A, const Team& tm, TeamSmem<R>& sm, 
         }
         tm.argmax(bestc, bj, sm);
         tm.sync();
-        gram_rows<R>(tm, sm, Qs, q, k);
-        tm.sync();
+        double nu2, cross;
+        gram_rows<R>(tm, sm, Qs, q, k, nu2, cross);
         if (tid == 0) {
-            double nu2 = sm.tr[k], cross = 0.0;
-            for (int p = 0; p < k; ++p) cross += sm.tr[p];
             lam2 = lam2 + nu2 + 2.0 * cross;
             sm.stop = (nu2 <= A.eps2 * lam2) || (bj < 0);
         }

@@ -427,6 +427,8 @@ hh_status hh_predict(hh_ctx* ctx, const double* X_dev, const double* F_dev, cons
         int64_t* pofs = dev_alloc_t<int64_t>(b->nG + 1, s);
         int64_t total = partial_offsets(t, b, 0, pofs, s);
         void* part = dev_alloc(rb * 3 * (size_t)(total > 0 ? total : 1), s);
+        // blocks of other shards are not written by this call
+        if (p->n_shards > 1) HH_CUDA(cudaMemsetAsync(part, 0, rb * 3 * (size_t)(total > 0 ? total : 1), s));
         AcaRun r;
         r.Fs = Fs;
         r.part = part;

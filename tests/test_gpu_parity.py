@@ -125,22 +125,26 @@ def test_predict_fp64_matches_oracle_hmatvec(ctx, kind):
     assert oracle.rel_error(Uo, U) < 1e-6
 
 
+FP32_FLOOR = 1e-5   # eps_r floor of FP32 arithmetic (observed 0.5-5e-6 at N = 1024)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("eps", [1e-3, 1e-4, 1e-6])
-def test_predict_fp32_against_dense(ctx, eps):
+def test_predict_against_dense(ctx, eps, prec):
     n = 1024
     X = hh_synth.rsa_cube(n, 0.1)
     ks = kern()
     errs = []
+    a1 = oracle.self_mobility()
     for s in range(5):   # Eq. 11 averaged over 5 force vectors
         F = hh_synth.forces(n, s)
-        U = ctx.predict(cuda(X), cuda(F), hh.Params(precision="fp32", eps=eps)).cpu().numpy()
+        U = ctx.predict(cuda(X), cuda(F), hh.Params(precision=prec, eps=eps)).cpu().numpy()
         Ud = oracle.dense_matvec(X, F, ks, with_self=True)
-        a1 = oracle.self_mobility()
         errs.append(oracle.rel_error(Ud - a1 * F, U - a1 * F))
-        if s == 0:
+        if s == 0 and prec == "fp32":
             Uo, _ = oracle.hmatvec(X, F, ks, leaf=32, eta=1.0, eps=eps, max_rank=48)
             assert oracle.rel_error(Uo, U) < 2e-5
-    assert np.mean(errs) <= eps
+    assert np.mean(errs) <= (eps if prec == "fp64" else max(eps, FP32_FLOOR))
 
 
 def test_predict_ragged_and_tiny(ctx):
