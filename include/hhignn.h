@@ -139,6 +139,25 @@ hh_status hh_matvec(hh_ctx *ctx, const hh_hmat *h, const double *F_dev, double *
 hh_status hh_predict(hh_ctx *ctx, const double *X_dev, const double *F_dev, const int64_t *offsets,
                      int32_t batch, const hh_params *p, void *stream, double *U_dev);
 
+/* Allocation-free product of one block (the paper has no counterpart; it is
+ * a service for callers that may not allocate device memory when they call,
+ * e.g. an application whose device memory is all handed to its own pool, or
+ * a real-time step that must not risk the synchronisation or failure of a
+ * cudaMalloc).  y_dev [c, 3] FP64 = C (Q F) where C Q is the Algorithm 2
+ * approximation (p->eps, p->max_rank, p->j1_rule, p->precision, p->kernel) of
+ * the block G(m, n) = K(Xt_m - Xs_n); Xt_dev [c, 3], Xs_dev [q, 3], F_dev
+ * [q, 3] FP64 device, caller-owned; rank_dev (int32, may be NULL) receives the
+ * rank.  1 <= c, q <= 128 and max_rank <= 64, else HH_ERR_ARG.  Every
+ * temporary lives in one fixed 1.2 MB device array inside the library, held
+ * by every GPU that loads it until exit: the call allocates nothing.  The
+ * first call on a device looks up that array's address (make it before any
+ * stream capture).  Calls share the array: two calls that overlap on the GPU
+ * race.  ctx must have been created (and hh_set_mlp called for the MLP
+ * kernel) beforehand; the call is asynchronous on stream. */
+hh_status hh_aca_block_apply_noalloc(hh_ctx *ctx, const double *Xt_dev, int32_t c, const double *Xs_dev, int32_t q,
+                                     const double *F_dev, const hh_params *p, void *stream, double *y_dev,
+                                     int32_t *rank_dev);
+
 /* Adjoint of L = sum_i gU_i . U_i for U = alpha_1 F + M_H F built by hh_aca
  * with the MLP kernel: gF_dev = alpha_1 gU + M_H^T gU (FP64 [N,3]),
  * gX_dev += dL/dX (FP64 [N,3]) and gtheta_dev += dL/dtheta (float32, length

@@ -33,6 +33,7 @@ EXPORTS = [
     "hh_default_params", "hh_create", "hh_destroy", "hh_last_error", "hh_set_mlp", "hh_build_tree",
     "hh_partition", "hh_aca", "hh_matvec", "hh_predict", "hh_matvec_backward", "hh_export_tree",
     "hh_export_blocks", "hh_export_aca", "hh_stats", "hh_tree_free", "hh_blocks_free", "hh_hmat_free",
+    "hh_aca_block_apply_noalloc",
 ]
 
 
@@ -90,6 +91,7 @@ def lib():
             "hh_tree_free": (None, [_P]),
             "hh_blocks_free": (None, [_P]),
             "hh_hmat_free": (None, [_P]),
+            "hh_aca_block_apply_noalloc": (st, [_P, _P, i32, _P, i32, _P, _P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)

@@ -756,3 +756,54 @@ void lowrank_apply(hh_ctx* ctx, const hh_hmat* h, const double* Fs, void* part, 
                                             h->tree->nbeg, h->tree->nend, Fs, (float*)part, pofs, transpose);
     HH_CHECK_LAUNCH();
 }
+
+// One admissible block, ACA fused with the low-rank apply, on caller-provided
+// device memory (used by the allocation-free entry point): positions Xs
+// [c+q, 3] (targets first), forces Fs [c+q, 3], the one-block lists PG / nbeg
+// / nend / work / pofs, a zeroed work counter, the team workspace ws (one
+// warp team; every warp of the launch shares it, only the one that takes the
+// block touches it), the partial output part [c, 3] and rank[0].
+void aca_single_block_ws(hh_ctx* ctx, const hh_params& p, int32_t c, int32_t q, const double* Xs, const double* Fs,
+                         const int32_t* PG, const int32_t* nbeg, const int32_t* nend, const int32_t* work,
+                         unsigned long long* counter, void* ws, void* part, const int64_t* pofs, int32_t* rank,
+                         cudaStream_t s)
+{
+    HH_REQUIRE(c >= 1 && q >= 1 && c <= SMALL_MAX && q <= SMALL_MAX, HH_ERR_ARG, "block sides must be in [1, 128]");
+    auto go = [&](auto tag) {
+        using R = decltype(tag);
+        AcaArgs<R> A{};
+        A.Xs = Xs;
+        A.th_g = theta_for<R>(ctx, p, &A.n_th);
+        A.pp = PairParams{p.radius, p.viscosity};
+        A.Fs = Fs;
+        A.PG = PG;
+        A.nbeg = nbeg;
+        A.nend = nend;
+        A.work = work;
+        A.n_work = 1;
+        A.counter = counter;
+        A.max_rank = p.max_rank;
+        A.eps2 = p.eps * p.eps;
+        A.j1_rule = p.j1_rule;
+        A.seed = p.seed;
+        A.scratch = (R*)ws;
+        A.team_stride = 0;
+        A.rank = rank;
+        A.part = (R*)part;
+        A.pofs = pofs;
+        A.status = ctx->d_status;
+        A.n_queries = ctx->d_counters + 4;
+        const size_t smem = WPB * sizeof(TeamSmem<R>) + (size_t)A.n_th * sizeof(R);
+        const int kind = kernel_kind(p, ctx->width);
+        auto launch = [&](auto kern) {
+            HH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<1, 32 * WPB, smem, s>>>(A, 0);
+            HH_CHECK_LAUNCH();
+        };
+        if (kind == 0) launch(k_aca_warp<R, 0>);
+        else if (kind == 1) launch(k_aca_warp<R, 1>);
+        else launch(k_aca_warp<R, 2>);
+    };
+    if (p.precision == HH_FP64) go(double{});
+    else go(float{});
+}

@@ -131,6 +131,8 @@ __global__ void k_fac_len(const int32_t* __restrict__ PG, int64_t nG, const int3
 
 }  // namespace
 
+void check_params_public(const hh_ctx* ctx, const hh_params* p) { check_params(ctx, p); }
+
 void free_hmat(hh_hmat* h)
 {
     if (!h) return;

@@ -124,6 +124,14 @@ struct AcaRun {
 void aca_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_params& p, const AcaRun& r,
              cudaStream_t s);
 
+// Fused ACA + apply of one block on caller-provided workspace (no allocation).
+void aca_single_block_ws(hh_ctx* ctx, const hh_params& p, int32_t c, int32_t q, const double* Xs, const double* Fs,
+                         const int32_t* PG, const int32_t* nbeg, const int32_t* nend, const int32_t* work,
+                         unsigned long long* counter, void* ws, void* part, const int64_t* pofs, int32_t* rank,
+                         cudaStream_t s);
+// Parameter checks shared by the entry points (hh_api.cu).
+void check_params_public(const hh_ctx* ctx, const hh_params* p);
+
 // Low-rank apply from stored factors into per-block partials.
 void lowrank_apply(hh_ctx* ctx, const hh_hmat* h, const double* Fs, void* part, const int64_t* pofs, int transpose,
                    cudaStream_t s);
