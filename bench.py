@@ -156,7 +156,7 @@ def run_ours(args, rank, world):
     ctx = hh.Context(dev)
     ctx.set_mlp(theta, 32)
     prec = args.precision
-    p = hh.Params(leaf_size=32, eta=1.0, eps=args.eps, max_rank=48, precision=prec)
+    p = hh.Params(leaf_size=args.leaf, eta=1.0, eps=args.eps, max_rank=48, precision=prec)
     Xd = torch.as_tensor(X).cuda()
     Fd = torch.as_tensor(F).cuda()
     U = torch.empty_like(Xd)
@@ -231,7 +231,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": "particle-velocities/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else prec, "data": "synthetic",
-        "config": {"workload": f"uniform_cube_rsa_N{n}_phi0.1_mlp4-32-32-32-6", "n": n, "leaf_size": 32,
+        "config": {"workload": f"uniform_cube_rsa_N{n}_phi0.1_mlp4-32-32-32-6", "n": n, "leaf_size": args.leaf,
                    "eta": 1.0, "eps": args.eps, "max_rank": 48, "precision": prec,
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"independent suspension per GPU"},
         "rel_err": rel_err, "rel_err_rows": len(idx),
@@ -262,6 +262,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--leaf", type=int, default=32)
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=64)
