@@ -187,6 +187,19 @@ def filaments(n_chains: int, beads: int, bond: float = 2.2, a: float = 1.0, phi:
         side *= 1.05
 
 
+def two_particle_samples(batch: int, seed: int, dmin: float = 2.0, dmax: float = 1000.0):
+    """Training configurations of two particles (Section 2.3): separation
+    r = x_1 - x_2 with |r| log-uniform in [dmin, dmax] and uniform direction,
+    and a unit force on particle 2 drawn from {e_x, e_y, e_z}.  Returns
+    (r [B,3], e [B,3]) float64."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u = rng.standard_normal((batch, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    d = np.exp(rng.uniform(np.log(dmin), np.log(dmax), size=batch))
+    e = np.eye(3)[rng.integers(0, 3, size=batch)]
+    return u * d[:, None], e
+
+
 def forces(n: int, seed: int) -> np.ndarray:
     """i.i.d. N(0,1) force components, shape [n, 3], float64."""
     rng = np.random.Generator(np.random.PCG64(seed))

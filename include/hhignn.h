@@ -139,6 +139,34 @@ hh_status hh_matvec(hh_ctx *ctx, const hh_hmat *h, const double *F_dev, double *
 hh_status hh_predict(hh_ctx *ctx, const double *X_dev, const double *F_dev, const int64_t *offsets,
                      int32_t batch, const hh_params *p, void *stream, double *U_dev);
 
+/* The pair kernel of Eq. 4 (or RPY) for n separations: K_dev [n, 9] FP64
+ * (row-major 3x3 per pair) = K(r_i), r_dev [n, 3] FP64 (r = x_target -
+ * x_source, non-zero), in the arithmetic of p->precision (HH_BF16: the
+ * tensor-core MLP used by the BF16 near field).  Asynchronous on stream. */
+hh_status hh_eval_pairs(hh_ctx *ctx, const double *r_dev, int64_t n, const hh_params *p, void *stream,
+                        double *K_dev);
+
+/* Training loss of Eq. 5 (Section 2.3) and its gradient for a batch of
+ * two-particle samples: r_dev [B, 3] separations (particle 1 minus particle
+ * 2), e_dev [B, 3] unit forces on particle 2, U_dev [B, 3] teacher velocities
+ * of particle 1 (NULL: the closed-form RPY velocity with radius a and
+ * mu = 1, the stand-in for the paper's Stokesian-dynamics data); all FP64
+ * device.  theta_dev: float32 packed parameters of 4 -> width -> width ->
+ * width -> 6.  *loss (host) = (1/B) sum |U - K(r) e|^2 / |U|^2 with
+ * K = S(MLP(f)) / |r|; grad_dev (float32, may be NULL) = dL/dtheta, summed in
+ * sample order (reproducible).  Synchronises the stream. */
+hh_status hh_train_loss_grad(hh_ctx *ctx, const float *theta_dev, int width, const double *r_dev,
+                             const double *e_dev, const double *U_dev, int64_t batch, double radius,
+                             float *grad_dev, void *stream, double *loss);
+
+/* One training step: the loss and gradient above, then Adam (beta1 = 0.9,
+ * beta2 = 0.999, eps = 1e-8, bias-corrected with step count step >= 1) on
+ * theta_dev, m_dev, v_dev (float32, length of theta, caller-owned; zero m and
+ * v before step 1).  *loss is the loss before the update. */
+hh_status hh_train_step(hh_ctx *ctx, float *theta_dev, float *m_dev, float *v_dev, int64_t step, int width,
+                        const double *r_dev, const double *e_dev, const double *U_dev, int64_t batch,
+                        double radius, double lr, void *stream, double *loss);
+
 /* Allocation-free product of one block (the paper has no counterpart; it is
  * a service for callers that may not allocate device memory when they call,
  * e.g. an application whose device memory is all handed to its own pool, or

@@ -33,7 +33,7 @@ EXPORTS = [
     "hh_default_params", "hh_create", "hh_destroy", "hh_last_error", "hh_set_mlp", "hh_build_tree",
     "hh_partition", "hh_aca", "hh_matvec", "hh_predict", "hh_matvec_backward", "hh_export_tree",
     "hh_export_blocks", "hh_export_aca", "hh_stats", "hh_tree_free", "hh_blocks_free", "hh_hmat_free",
-    "hh_aca_block_apply_noalloc",
+    "hh_aca_block_apply_noalloc", "hh_eval_pairs", "hh_train_loss_grad", "hh_train_step",
 ]
 
 
@@ -92,6 +92,10 @@ def lib():
             "hh_blocks_free": (None, [_P]),
             "hh_hmat_free": (None, [_P]),
             "hh_aca_block_apply_noalloc": (st, [_P, _P, i32, _P, i32, _P, _P, _P, _P, _P]),
+            "hh_eval_pairs": (st, [_P, _P, i64, _P, _P, _P]),
+            "hh_train_loss_grad": (st, [_P, _P, ctypes.c_int, _P, _P, _P, i64, ctypes.c_double, _P, _P, _P]),
+            "hh_train_step": (st, [_P, _P, _P, _P, i64, ctypes.c_int, _P, _P, _P, i64, ctypes.c_double,
+                                   ctypes.c_double, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -174,6 +178,35 @@ class Context:
                               ctypes.byref(params), _stream(stream), _dptr(U))
         self.last_status = self._check(st, "hh_predict")
         return U
+
+    def eval_pairs(self, r, params: CParams, stream=None):
+        """K(r) [n, 3, 3] for separations r [n, 3] (float64 CUDA) in the params' precision."""
+        import torch
+        _check_xyz(r, "r")
+        K = torch.empty((r.shape[0], 9), dtype=torch.float64, device=r.device)
+        self._check(lib().hh_eval_pairs(self._h, _dptr(r), r.shape[0], ctypes.byref(params), _stream(stream),
+                                        _dptr(K)), "hh_eval_pairs")
+        return K.view(-1, 3, 3)
+
+    # -- training (Eq. 5) -------------------------------------------------------
+    def train_loss_grad(self, theta, width, r, e, U=None, radius=1.0, grad=True, stream=None):
+        """(loss, grad) of Eq. 5 on the GPU; theta float32 CUDA, r/e/U float64 [B,3] CUDA."""
+        import torch
+        g = torch.empty_like(theta) if grad else None
+        loss = ctypes.c_double()
+        self._check(lib().hh_train_loss_grad(self._h, _dptr(theta), width, _dptr(r), _dptr(e),
+                                             _dptr(U) if U is not None else None, r.shape[0], radius,
+                                             _dptr(g) if g is not None else None, _stream(stream),
+                                             ctypes.byref(loss)), "hh_train_loss_grad")
+        return loss.value, g
+
+    def train_step(self, theta, m, v, step, width, r, e, U=None, radius=1.0, lr=1e-3, stream=None):
+        """One Adam step in place on theta, m, v (float32 CUDA); returns the loss before the step."""
+        loss = ctypes.c_double()
+        self._check(lib().hh_train_step(self._h, _dptr(theta), _dptr(m), _dptr(v), step, width, _dptr(r), _dptr(e),
+                                        _dptr(U) if U is not None else None, r.shape[0], radius, lr,
+                                        _stream(stream), ctypes.byref(loss)), "hh_train_step")
+        return loss.value
 
     def stats(self) -> dict:
         s = CStats()

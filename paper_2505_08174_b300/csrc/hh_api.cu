@@ -52,8 +52,9 @@ void check_params(const hh_ctx* ctx, const hh_params* p)
     HH_REQUIRE(p->max_rank >= 1 && p->max_rank <= 64, HH_ERR_ARG, "max_rank must be in [1, 64]");
     HH_REQUIRE(p->precision == HH_FP64 || p->precision == HH_FP32 || p->precision == HH_BF16, HH_ERR_ARG,
                "unknown precision");
-    HH_REQUIRE(p->precision != HH_BF16, HH_ERR_ARG, "precision HH_BF16 is not available in this build");
     HH_REQUIRE(p->kernel == HH_MLP || p->kernel == HH_RPY, HH_ERR_ARG, "unknown kernel");
+    HH_REQUIRE(p->precision != HH_BF16 || p->kernel == HH_MLP, HH_ERR_ARG,
+               "precision HH_BF16 evaluates the MLP on tensor cores; use HH_FP32/HH_FP64 for HH_RPY");
     HH_REQUIRE(p->kernel == HH_RPY || ctx->n_theta > 0, HH_ERR_ARG, "MLP kernel requested but hh_set_mlp not called");
     HH_REQUIRE(p->radius > 0.0 && p->viscosity > 0.0, HH_ERR_ARG, "radius and viscosity must be > 0");
     HH_REQUIRE(p->n_shards >= 1 && p->shard_id >= 0 && p->shard_id < p->n_shards, HH_ERR_ARG, "bad shard");
@@ -467,6 +468,52 @@ hh_status hh_predict(hh_ctx* ctx, const double* X_dev, const double* F_dev, cons
     free_blocks(b);
     free_tree(t);
     return st;
+}
+
+hh_status hh_eval_pairs(hh_ctx* ctx, const double* r_dev, int64_t n, const hh_params* p, void* stream, double* K_dev)
+{
+    if (!ctx) return HH_ERR_ARG;
+    return guarded(ctx, [&]() {
+        check_params(ctx, p);
+        HH_REQUIRE(n >= 0 && (n == 0 || (r_dev && K_dev)), HH_ERR_ARG, "NULL argument");
+        cudaStream_t s = (cudaStream_t)stream;
+        if (p->precision == HH_BF16) eval_pairs_tc(ctx, r_dev, n, p->radius, K_dev, s);
+        else eval_pairs_simt(ctx, *p, r_dev, n, K_dev, s);
+        return HH_OK;
+    });
+}
+
+hh_status hh_train_loss_grad(hh_ctx* ctx, const float* theta_dev, int width, const double* r_dev, const double* e_dev,
+                             const double* U_dev, int64_t batch, double radius, float* grad_dev, void* stream,
+                             double* loss)
+{
+    if (!ctx) return HH_ERR_ARG;
+    return guarded(ctx, [&]() {
+        HH_REQUIRE(theta_dev && r_dev && e_dev && loss, HH_ERR_ARG, "NULL argument");
+        HH_REQUIRE(radius > 0.0, HH_ERR_ARG, "radius must be > 0");
+        *loss = train_loss_grad(ctx, theta_dev, width, r_dev, e_dev, U_dev, batch, radius, grad_dev,
+                                (cudaStream_t)stream);
+        return HH_OK;
+    });
+}
+
+hh_status hh_train_step(hh_ctx* ctx, float* theta_dev, float* m_dev, float* v_dev, int64_t step, int width,
+                        const double* r_dev, const double* e_dev, const double* U_dev, int64_t batch, double radius,
+                        double lr, void* stream, double* loss)
+{
+    if (!ctx) return HH_ERR_ARG;
+    return guarded(ctx, [&]() {
+        HH_REQUIRE(theta_dev && m_dev && v_dev && r_dev && e_dev && loss, HH_ERR_ARG, "NULL argument");
+        HH_REQUIRE(radius > 0.0 && lr > 0.0, HH_ERR_ARG, "radius and lr must be > 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        HH_REQUIRE(width == 32 || width == 64, HH_ERR_ARG, "width must be 32 or 64");
+        const int P = 4 * width + width + 2 * (width * width + width) + 6 * width + 6;
+        float* g = dev_alloc_t<float>(P, s);
+        *loss = train_loss_grad(ctx, theta_dev, width, r_dev, e_dev, U_dev, batch, radius, g, s);
+        adam_step(theta_dev, g, m_dev, v_dev, P, step, lr, 0.9, 0.999, 1e-8, s);
+        dev_free(g, s);
+        return HH_OK;
+    });
 }
 
 hh_status hh_matvec_backward(hh_ctx* ctx, const hh_hmat* h, const double* gU_dev, const double* F_dev, double* gF_dev,

@@ -124,6 +124,20 @@ struct AcaRun {
 void aca_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_params& p, const AcaRun& r,
              cudaStream_t s);
 
+// Tensor-core (tcgen05) MLP paths (hh_tcmlp.cu): near field in HH_BF16 mode
+// (work = target leaves) and K(r) for a list of separations.
+void near_field_tc(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_params& p, const double* Fs, float* y,
+                   const int32_t* work, int64_t n_work, int transpose, cudaStream_t s);
+void eval_pairs_tc(hh_ctx* ctx, const double* r, int64_t n, double a, double* K, cudaStream_t s);
+// SIMT K(r) for a list of separations (hh_near.cu), FP32 or FP64 per p.
+void eval_pairs_simt(hh_ctx* ctx, const hh_params& p, const double* r, int64_t n, double* K, cudaStream_t s);
+
+// Training of the pair MLP (hh_train.cu).
+double train_loss_grad(hh_ctx* ctx, const float* theta, int width, const double* r, const double* e, const double* U,
+                       int64_t B, double a, float* grad_dev, cudaStream_t s);
+void adam_step(float* theta, const float* g, float* m, float* v, int n, int64_t t, double lr, double b1, double b2,
+               double eps, cudaStream_t s);
+
 // Fused ACA + apply of one block on caller-provided workspace (no allocation).
 void aca_single_block_ws(hh_ctx* ctx, const hh_params& p, int32_t c, int32_t q, const double* Xs, const double* Fs,
                          const int32_t* PG, const int32_t* nbeg, const int32_t* nend, const int32_t* work,

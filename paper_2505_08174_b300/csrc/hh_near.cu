@@ -200,7 +200,9 @@ void near_field(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_para
     k_compact32<<<(unsigned)ceil_div(nn, 256), 256, 0, s>>>(flag, off, nn, work);
     HH_CHECK_LAUNCH();
     HH_CUDA(cudaMemsetAsync(y, 0, (size_t)real_bytes(p) * 3 * t->n, s));
-    if (n_work > 0) {
+    if (n_work > 0 && p.precision == HH_BF16) {
+        near_field_tc(ctx, t, b, p, Fs, (float*)y, work, n_work, transpose, s);
+    } else if (n_work > 0) {
         const int kind = kernel_kind(p, ctx->width);
         if (p.precision == HH_FP64) {
             if (kind == 0) launch_near<double, 0>(ctx, t, b, p, Fs, (double*)y, work, n_work, transpose, s);
@@ -216,6 +218,51 @@ void near_field(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_para
     dev_free(off, s);
     dev_free(tot, s);
     dev_free(work, s);
+}
+
+namespace {
+template <typename R, int KIND>
+__global__ void k_eval_pairs(const double* __restrict__ r, int64_t n, const R* __restrict__ th_g, int n_th,
+                             PairParams pp, double* __restrict__ K)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* th = reinterpret_cast<R*>(smem_raw);
+    for (int i = threadIdx.x; i < n_th; i += blockDim.x) th[i] = th_g[i];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        R k[9];
+        pair_block<R, KIND>(th, pp, (R)r[3 * i], (R)r[3 * i + 1], (R)r[3 * i + 2], k);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) K[9 * i + e] = (double)k[e];
+    }
+}
+
+template <typename R, int KIND>
+void launch_eval(hh_ctx* ctx, const hh_params& p, const double* r, int64_t n, double* K, cudaStream_t s)
+{
+    int n_th = 0;
+    const R* th = theta_for<R>(ctx, p, &n_th);
+    const size_t smem = sizeof(R) * (size_t)n_th;
+    HH_CUDA(cudaFuncSetAttribute(k_eval_pairs<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t blocks = std::min<int64_t>(ceil_div(n, 128), (int64_t)ctx->n_sm * 8);
+    k_eval_pairs<R, KIND><<<(unsigned)blocks, 128, smem, s>>>(r, n, th, n_th, PairParams{p.radius, p.viscosity}, K);
+    HH_CHECK_LAUNCH();
+}
+}  // namespace
+
+void eval_pairs_simt(hh_ctx* ctx, const hh_params& p, const double* r, int64_t n, double* K, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int kind = kernel_kind(p, ctx->width);
+    if (p.precision == HH_FP64) {
+        if (kind == 0) launch_eval<double, 0>(ctx, p, r, n, K, s);
+        else if (kind == 1) launch_eval<double, 1>(ctx, p, r, n, K, s);
+        else launch_eval<double, 2>(ctx, p, r, n, K, s);
+    } else {
+        if (kind == 0) launch_eval<float, 0>(ctx, p, r, n, K, s);
+        else if (kind == 1) launch_eval<float, 1>(ctx, p, r, n, K, s);
+        else launch_eval<float, 2>(ctx, p, r, n, K, s);
+    }
 }
 
 int64_t partial_offsets(const hh_tree* t, const hh_blocks* b, int transpose, int64_t* pofs, cudaStream_t s)

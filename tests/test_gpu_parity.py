@@ -247,3 +247,65 @@ def test_bad_arguments(ctx):
     with pytest.raises(hh.HHError) as e:
         ctx.predict(bad, X, hh.Params())
     assert e.value.status == hh.HH_ERR_NUMERIC
+
+
+# --------------------------------------------------------------------------
+# pair kernel element-wise, every precision (BF16 = tcgen05 tensor cores)
+# --------------------------------------------------------------------------
+# BF16 bound: features and activations are split into a bf16 part and a bf16
+# remainder (~16 significant bits, relative 2^-17 = 7.6e-6 each), weights are
+# exactly bf16, accumulation FP32: a few 1e-5 of the block scale per entry.
+PAIR_TOL = {"fp64": 1e-12, "fp32": 2e-6, "bf16": 1e-4}
+
+
+@pytest.mark.parametrize("width", [32, 64])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_eval_pairs_against_oracle(prec, width):
+    c = hh.Context()
+    th = THETA32 if width == 32 else THETA64
+    c.set_mlp(th, width)
+    rng = np.random.default_rng(17)
+    n = 3001                      # ragged: 23 full 128-pair tiles + 57
+    u = rng.normal(size=(n, 3)); u /= np.linalg.norm(u, axis=1)[:, None]
+    r = u * np.exp(rng.uniform(np.log(2.0), np.log(800.0), size=n))[:, None]
+    K = c.eval_pairs(cuda(r), hh.Params(precision=prec)).cpu().numpy()
+    k = kern("mlp", width)
+    Ko = np.stack([oracle.pair_block(k, ri) for ri in r])
+    scale = np.abs(Ko).reshape(n, 9).max(axis=1)
+    err = (np.abs(K - Ko).reshape(n, 9).max(axis=1) / scale).max()
+    assert err < PAIR_TOL[prec], f"{prec} w={width}: max relative entry error {err:.3e}"
+
+
+BF16_FLOOR = 1e-4   # eps_r floor of the BF16 tensor-core near field (see PAIR_TOL)
+
+
+def test_predict_bf16_against_oracle(ctx):
+    n = 2048
+    X = hh_synth.rsa_cube(n, 0.1, seed=6)
+    F = hh_synth.forces(n, 1)
+    U = ctx.predict(cuda(X), cuda(F), hh.Params(precision="bf16")).cpu().numpy()
+    Uo, _ = oracle.hmatvec(X, F, kern(), leaf=32, eta=1.0, eps=1e-4, max_rank=48)
+    assert oracle.rel_error(Uo, U) < 1e-4
+    a1 = oracle.self_mobility()
+    Ud = oracle.dense_matvec(X, F, kern(), with_self=False)
+    assert oracle.rel_error(Ud, U - a1 * F) < max(1e-4, BF16_FLOOR)
+
+
+def test_predict_bf16_width64_and_transpose(ctx):
+    c = hh.Context()
+    c.set_mlp(THETA64, 64)
+    n = 1500
+    X = hh_synth.rsa_cube(n, 0.1, seed=8)
+    F = hh_synth.forces(n, 2)
+    W = hh_synth.forces(n, 9)
+    p = hh.Params(precision="bf16", leaf_size=64)
+    U = c.predict(cuda(X), cuda(F), p).cpu().numpy()
+    Uo, _ = oracle.hmatvec(X, F, kern("mlp", 64), leaf=64, eta=1.0, eps=1e-4, max_rank=48)
+    assert oracle.rel_error(Uo, U) < 1e-4
+    t = c.build_tree(cuda(X), p)
+    h = c.aca(t, c.partition(t, p), p)
+    U1 = c.matvec(h, cuda(F)).cpu().numpy()
+    UT = c.matvec(h, cuda(W), transpose=True).cpu().numpy()
+    assert oracle.rel_error(U, U1) < 1e-6
+    # <W, M F> = <M^T W, F> holds to the BF16 pair-kernel noise of the two near-field sweeps
+    assert abs(np.sum(W * U1) - np.sum(UT * F)) <= 1e-4 * np.sqrt(np.sum(W * W) * np.sum(U1 * U1))
