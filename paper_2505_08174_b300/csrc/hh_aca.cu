@@ -260,127 +260,123 @@ __device__ void aca_block(const AcaArgs<R>& A, const Team& tm, TeamSmem<R>& sm, 
     double lam2 = 0.0;
     int k = 0;
     bool capped = false;
+    int bi = -1, bj = -1;
     while (k < kmax) {
-        // Q_p(j_k), p < k
-        for (int idx = tid; idx < k * 9; idx += SIZE) sm.qj[idx] = Qs[(int64_t)idx * q + j];
-        tm.sync();
-        // column residual (unscaled) and row-pivot candidates
-        R best = (R)-1;
-        int bi = -1;
+        bool done = false;  // uniform over the team
+        // pass 0 generates the column residual c_k over the rows m (line 4) and
+        // picks i_k (line 5), pivots and scales it (line 6); pass 1 generates the
+        // row residual q_k over the columns n (line 7), picks j_{k+1} (line 8)
+        // and updates the norms (lines 9-10).  Both passes share one pair-kernel
+        // call site, which keeps the kernel's instruction footprint small.
 #pragma unroll 1
-        for (int i = 0; i < ROWS; ++i) {
-            const int m = tid + SIZE * i;
-            if (m >= c) break;
-            R rx, ry, rz, K[9];
-            sep<R>(A.Xs, t0 + m, s0 + j, rx, ry, rz);
-            pair_block<R, KIND>(th, A.pp, rx, ry, rz, K);
-            for (int p = 0; p < k; ++p) {
-                R cp[9], t9[9];
-                ld9(Cs + (int64_t)p * 9 * c, c, m, cp);
-                mm3(cp, sm.qj + 9 * p, t9);
-#pragma unroll
-                for (int e = 0; e < 9; ++e) K[e] -= t9[e];
-            }
-            st9(Cs + (int64_t)k * 9 * c, c, m, K);
-            if (!is_used(usedR, fR, i, m)) {
-                R v = fro2(K);
-                if (v > best) { best = v; bi = m; }
-            }
-        }
-        tm.argmax(best, bi, sm);
-        if (bi < 0 || !(best > (R)0)) break;
-        tm.sync();
-        if (tid == 0) {
-            double P[9], Pi[9];
-#pragma unroll
-            for (int e = 0; e < 9; ++e) P[e] = (double)Cs[((int64_t)k * 9 + e) * c + bi];
-            double det = inv3d(P, Pi);
-            double rc = det != 0.0 ? 1.0 / sqrt(fro2(P) * fro2(Pi)) : 0.0;
-            int bad = !(det != 0.0) || !(rc >= 1e-10);
-            sm.flag = bad;
-            if (!bad)
-#pragma unroll
-                for (int e = 0; e < 9; ++e) sm.Pi[e] = (R)Pi[e];
-        }
-        tm.sync();
-        if (sm.flag) {
-            double bd = 0.0;
-            int bj = -1;
+        for (int pass = 0; pass < 2; ++pass) {
+            const int nx = pass == 0 ? c : q;
+            R* fac = pass == 0 ? Cs : Qs;       // factor being extended (rows x)
+            R* line = fac + (int64_t)k * 9 * nx;
+            R* piv = pass == 0 ? sm.qj : sm.ci;  // Q_p(j_k) or C_p(i_k), p < k
+            for (int idx = tid; idx < k * 9; idx += SIZE)
+                piv[idx] = pass == 0 ? Qs[(int64_t)idx * q + j] : Cs[(int64_t)idx * c + bi];
+            tm.sync();
+            R best = (R)-1;
+            int barg = -1;
+#pragma unroll 1
             for (int i = 0; i < ROWS; ++i) {
-                const int m = tid + SIZE * i;
-                if (m >= c) break;
-                if (is_used(usedR, fR, i, m)) continue;
-                double P[9];
+                const int x = tid + SIZE * i;
+                if (x >= nx) break;
+                R rx, ry, rz, K[9];
+                sep<R>(A.Xs, pass == 0 ? t0 + x : t0 + bi, pass == 0 ? s0 + j : s0 + x, rx, ry, rz);
+                pair_block<R, KIND>(th, A.pp, rx, ry, rz, K);
+                for (int p = 0; p < k; ++p) {
+                    R v[9], t9[9];
+                    ld9(fac + (int64_t)p * 9 * nx, nx, x, v);
+                    if (pass == 0) mm3(v, piv + 9 * p, t9);   // C_p(m) Q_p(j_k)
+                    else mm3(piv + 9 * p, v, t9);             // C_p(i_k) Q_p(n)
 #pragma unroll
-                for (int e = 0; e < 9; ++e) P[e] = (double)Cs[((int64_t)k * 9 + e) * c + m];
-                double dv = fabs(det3d(P));
-                if (dv > bd) { bd = dv; bj = m; }
+                    for (int e = 0; e < 9; ++e) K[e] -= t9[e];
+                }
+                st9(line, nx, x, K);
+                const bool used = pass == 0 ? is_used(usedR, fR, i, x) : is_used(usedC, fC, i, x);
+                if (!used) {
+                    R v = fro2(K);
+                    if (v > best) { best = v; barg = x; }
+                }
             }
-            tm.argmax(bd, bj, sm);
-            if (bj < 0) break;
-            bi = bj;
+            tm.argmax(best, barg, sm);
+            if (pass == 1) {
+                bj = barg;
+                tm.sync();
+                double nu2, cross;
+                gram_rows<R>(tm, sm, Qs, q, k, nu2, cross);
+                if (tid == 0) {
+                    lam2 = lam2 + nu2 + 2.0 * cross;
+                    sm.stop = (nu2 <= A.eps2 * lam2) || (bj < 0);
+                }
+                tm.sync();
+                break;
+            }
+            if (barg < 0 || !(best > (R)0)) { done = true; break; }
+            bi = barg;
+            tm.sync();
             if (tid == 0) {
                 double P[9], Pi[9];
 #pragma unroll
                 for (int e = 0; e < 9; ++e) P[e] = (double)Cs[((int64_t)k * 9 + e) * c + bi];
-                inv3d(P, Pi);
+                double det = inv3d(P, Pi);
+                double rc = det != 0.0 ? 1.0 / sqrt(fro2(P) * fro2(Pi)) : 0.0;
+                int bad = !(det != 0.0) || !(rc >= 1e-10);
+                sm.flag = bad;
+                if (!bad)
 #pragma unroll
-                for (int e = 0; e < 9; ++e) sm.Pi[e] = (R)Pi[e];
+                    for (int e = 0; e < 9; ++e) sm.Pi[e] = (R)Pi[e];
             }
             tm.sync();
-        }
-        set_used(usedR, fR, bi);
-        if (tid == 0 && A.pivI) {
-            A.pivI[b * A.max_rank + k] = bi;
-            A.pivJ[b * A.max_rank + k] = j;
-        }
-        // c_k <- c_k [c_k(i_k)]^-1
-        R Pi[9];
+            if (sm.flag) {
+                double bd = 0.0;
+                int bdi = -1;
+                for (int i = 0; i < ROWS; ++i) {
+                    const int m = tid + SIZE * i;
+                    if (m >= c) break;
+                    if (is_used(usedR, fR, i, m)) continue;
+                    double P[9];
 #pragma unroll
-        for (int e = 0; e < 9; ++e) Pi[e] = sm.Pi[e];
-        for (int i = 0; i < ROWS; ++i) {
-            const int m = tid + SIZE * i;
-            if (m >= c) break;
-            R r[9], o[9];
-            ld9(Cs + (int64_t)k * 9 * c, c, m, r);
-            mm3(r, Pi, o);
-            st9(Cs + (int64_t)k * 9 * c, c, m, o);
-        }
-        tm.sync();
-        gram_cols<R>(tm, sm, Cs, c, k);
-        for (int idx = tid; idx < k * 9; idx += SIZE) sm.ci[idx] = Cs[(int64_t)idx * c + bi];
-        tm.sync();
-        // row residual and column-pivot candidates
-        R bestc = (R)-1;
-        int bj = -1;
-        for (int i = 0; i < ROWS; ++i) {
-            const int n = tid + SIZE * i;
-            if (n >= q) break;
-            R rx, ry, rz, K[9];
-            sep<R>(A.Xs, t0 + bi, s0 + n, rx, ry, rz);
-            pair_block<R, KIND>(th, A.pp, rx, ry, rz, K);
-            for (int p = 0; p < k; ++p) {
-                R qp[9], t9[9];
-                ld9(Qs + (int64_t)p * 9 * q, q, n, qp);
-                mm3(sm.ci + 9 * p, qp, t9);
+                    for (int e = 0; e < 9; ++e) P[e] = (double)Cs[((int64_t)k * 9 + e) * c + m];
+                    double dv = fabs(det3d(P));
+                    if (dv > bd) { bd = dv; bdi = m; }
+                }
+                tm.argmax(bd, bdi, sm);
+                if (bdi < 0) { done = true; break; }
+                bi = bdi;
+                if (tid == 0) {
+                    double P[9], Pi[9];
 #pragma unroll
-                for (int e = 0; e < 9; ++e) K[e] -= t9[e];
+                    for (int e = 0; e < 9; ++e) P[e] = (double)Cs[((int64_t)k * 9 + e) * c + bi];
+                    inv3d(P, Pi);
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) sm.Pi[e] = (R)Pi[e];
+                }
+                tm.sync();
             }
-            st9(Qs + (int64_t)k * 9 * q, q, n, K);
-            if (!is_used(usedC, fC, i, n)) {
-                R v = fro2(K);
-                if (v > bestc) { bestc = v; bj = n; }
+            set_used(usedR, fR, bi);
+            if (tid == 0 && A.pivI) {
+                A.pivI[b * A.max_rank + k] = bi;
+                A.pivJ[b * A.max_rank + k] = j;
             }
+            // c_k <- c_k [c_k(i_k)]^-1
+            R Pi[9];
+#pragma unroll
+            for (int e = 0; e < 9; ++e) Pi[e] = sm.Pi[e];
+            for (int i = 0; i < ROWS; ++i) {
+                const int m = tid + SIZE * i;
+                if (m >= c) break;
+                R r[9], o[9];
+                ld9(line, c, m, r);
+                mm3(r, Pi, o);
+                st9(line, c, m, o);
+            }
+            tm.sync();
+            gram_cols<R>(tm, sm, Cs, c, k);
         }
-        tm.argmax(bestc, bj, sm);
-        tm.sync();
-        double nu2, cross;
-        gram_rows<R>(tm, sm, Qs, q, k, nu2, cross);
-        if (tid == 0) {
-            lam2 = lam2 + nu2 + 2.0 * cross;
-            sm.stop = (nu2 <= A.eps2 * lam2) || (bj < 0);
-        }
-        tm.sync();
+        if (done) break;
         ++k;
         const bool stop = sm.stop;
         tm.sync();

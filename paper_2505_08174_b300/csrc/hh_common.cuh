@@ -145,32 +145,26 @@ __device__ __forceinline__ void mlp_f32(const float* __restrict__ th, const floa
     }
 #pragma unroll
     for (int j = 0; j < W; ++j) h[j] = silu_f(h[j]);
+    // layers 2 and 3 share one (looped) body: half the code, which matters
+    // for the instruction cache of the large ACA kernels
+#pragma unroll 1
+    for (int l = 0; l < 2; ++l) {
+        const float* Wl = l == 0 ? W2 : W3;
+        const float* bl = l == 0 ? b2 : b3;
 #pragma unroll
-    for (int j = 0; j < W; ++j) g[j] = b2[j];
+        for (int j = 0; j < W; ++j) g[j] = bl[j];
 #pragma unroll
-    for (int i = 0; i < W; ++i) {
-        const float x = h[i];
+        for (int i = 0; i < W; ++i) {
+            const float x = h[i];
 #pragma unroll
-        for (int j = 0; j < W; j += 4) {
-            const float4 w4 = *reinterpret_cast<const float4*>(W2 + i * W + j);
-            g[j] += w4.x * x; g[j + 1] += w4.y * x; g[j + 2] += w4.z * x; g[j + 3] += w4.w * x;
+            for (int j = 0; j < W; j += 4) {
+                const float4 w4 = *reinterpret_cast<const float4*>(Wl + i * W + j);
+                g[j] += w4.x * x; g[j + 1] += w4.y * x; g[j + 2] += w4.z * x; g[j + 3] += w4.w * x;
+            }
         }
+#pragma unroll
+        for (int j = 0; j < W; ++j) h[j] = silu_f(g[j]);
     }
-#pragma unroll
-    for (int j = 0; j < W; ++j) g[j] = silu_f(g[j]);
-#pragma unroll
-    for (int j = 0; j < W; ++j) h[j] = b3[j];
-#pragma unroll
-    for (int i = 0; i < W; ++i) {
-        const float x = g[i];
-#pragma unroll
-        for (int j = 0; j < W; j += 4) {
-            const float4 w4 = *reinterpret_cast<const float4*>(W3 + i * W + j);
-            h[j] += w4.x * x; h[j + 1] += w4.y * x; h[j + 2] += w4.z * x; h[j + 3] += w4.w * x;
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < W; ++j) h[j] = silu_f(h[j]);
     float oo[6] = {b4[0], b4[1], b4[2], b4[3], b4[4], b4[5]};
 #pragma unroll
     for (int i = 0; i < W; ++i) {
