@@ -31,7 +31,7 @@
 namespace {
 
 constexpr int MAXR = 64;          // hard cap on max_rank
-constexpr int WARP_ROWS = 4;      // warp team: up to 128 rows / columns per block
+constexpr int WARP_ROWS = 16;     // warp team: up to 512 rows / columns per block
 constexpr int CTA_T = 256;        // CTA team size
 constexpr int SMALL_MAX = 32 * WARP_ROWS;
 
@@ -222,8 +222,8 @@ __device__ void gram_rows(const Team& tm, TeamSmem<R>& sm, const R* Qs, int q, i
 
 // ---- the per-block ACA -----------------------------------------------------
 template <typename R, int KIND, class Team>
-__device__ void aca_block(const AcaArgs<R>& A, const Team& tm, TeamSmem<R>& sm, const R* th, R* Cs_base, int64_t b,
-                          int mode)
+__device__ void aca_block(const AcaArgs<R>& A, const Team& tm, TeamSmem<R>& sm, const R* th, R* hs, R* Cs_base,
+                          int64_t b, int mode)
 {
     constexpr int ROWS = Team::ROWS, SIZE = Team::SIZE;
     constexpr int NB = Team::REG_FLAGS ? (ROWS + 31) / 32 : 1;
@@ -285,7 +285,7 @@ __device__ void aca_block(const AcaArgs<R>& A, const Team& tm, TeamSmem<R>& sm, 
                 if (x >= nx) break;
                 R rx, ry, rz, K[9];
                 sep<R>(A.Xs, pass == 0 ? t0 + x : t0 + bi, pass == 0 ? s0 + j : s0 + x, rx, ry, rz);
-                pair_block<R, KIND>(th, A.pp, rx, ry, rz, K);
+                pair_block<R, KIND>(th, A.pp, rx, ry, rz, K, hs);
                 for (int p = 0; p < k; ++p) {
                     R v[9], t9[9];
                     ld9(fac + (int64_t)p * 9 * nx, nx, x, v);
@@ -454,6 +454,8 @@ __global__ void __launch_bounds__(32 * WPB) k_aca_warp(AcaArgs<R> A, int mode)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TeamSmem<R>* sms = reinterpret_cast<TeamSmem<R>*>(smem_raw);
     R* th = reinterpret_cast<R*>(smem_raw + sizeof(TeamSmem<R>) * WPB);
+    constexpr int ACT = act_floats_per_warp<R, KIND>();
+    R* hs = th + A.n_th + (threadIdx.x >> 5) * ACT + (threadIdx.x & 31);
     load_theta(A, th);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     TeamSmem<R>& sm = sms[w];
@@ -465,7 +467,7 @@ __global__ void __launch_bounds__(32 * WPB) k_aca_warp(AcaArgs<R> A, int mode)
         if (lane == 0) wi = atomicAdd(A.counter, 1ull);
         wi = __shfl_sync(0xffffffffu, wi, 0);
         if ((int64_t)wi >= A.n_work) break;
-        aca_block<R, KIND>(A, tm, sm, th, Cs, A.work[wi], mode);
+        aca_block<R, KIND>(A, tm, sm, th, hs, Cs, A.work[wi], mode);
     }
 }
 
@@ -475,6 +477,8 @@ __global__ void __launch_bounds__(CTA_T) k_aca_cta(AcaArgs<R> A, int mode)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TeamSmem<R>& sm = *reinterpret_cast<TeamSmem<R>*>(smem_raw);
     R* th = reinterpret_cast<R*>(smem_raw + sizeof(TeamSmem<R>));
+    constexpr int ACT = act_floats_per_warp<R, KIND>();
+    R* hs = th + A.n_th + (threadIdx.x >> 5) * ACT + (threadIdx.x & 31);
     __shared__ unsigned long long wi_s;
     load_theta(A, th);
     R* Cs = A.scratch + (int64_t)blockIdx.x * A.team_stride;
@@ -485,7 +489,7 @@ __global__ void __launch_bounds__(CTA_T) k_aca_cta(AcaArgs<R> A, int mode)
         unsigned long long wi = wi_s;
         __syncthreads();
         if ((int64_t)wi >= A.n_work) break;
-        aca_block<R, KIND>(A, tm, sm, th, Cs, A.work[wi], mode);
+        aca_block<R, KIND>(A, tm, sm, th, hs, Cs, A.work[wi], mode);
     }
 }
 
@@ -557,7 +561,7 @@ void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_
         B.n_work = n_large;
         B.scratch = scratch;
         B.team_stride = stride;
-        size_t smem = sizeof(TeamSmem<R>) + th_bytes;
+        size_t smem = sizeof(TeamSmem<R>) + th_bytes + sizeof(R) * act_floats_per_warp<R, KIND>() * (CTA_T / 32);
         HH_CUDA(cudaFuncSetAttribute(k_aca_cta<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         HH_CUDA(cudaEventRecord(ctx->kev[0], s));
         k_aca_cta<R, KIND><<<(unsigned)teams, CTA_T, smem, s>>>(B, mode);
@@ -578,7 +582,7 @@ void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_
         B.counter = A.counter + 1;
         B.scratch = scratch;
         B.team_stride = stride;
-        size_t smem = WPB * sizeof(TeamSmem<R>) + th_bytes;
+        size_t smem = WPB * sizeof(TeamSmem<R>) + th_bytes + sizeof(R) * act_floats_per_warp<R, KIND>() * WPB;
         HH_CUDA(cudaFuncSetAttribute(k_aca_warp<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         HH_CUDA(cudaEventRecord(ctx->kev[2], s));
         k_aca_warp<R, KIND><<<(unsigned)blocks, 32 * WPB, smem, s>>>(B, mode);
@@ -789,8 +793,10 @@ void aca_single_block_ws(hh_ctx* ctx, const hh_params& p, int32_t c, int32_t q, 
         A.pofs = pofs;
         A.status = ctx->d_status;
         A.n_queries = ctx->d_counters + 4;
-        const size_t smem = WPB * sizeof(TeamSmem<R>) + (size_t)A.n_th * sizeof(R);
+        const size_t smem0 = WPB * sizeof(TeamSmem<R>) + (size_t)A.n_th * sizeof(R);
         const int kind = kernel_kind(p, ctx->width);
+        const size_t act = kind == 2 ? 0 : (kind == 1 ? act_floats_per_warp<R, 1>() : act_floats_per_warp<R, 0>());
+        const size_t smem = smem0 + sizeof(R) * act * WPB;
         auto launch = [&](auto kern) {
             HH_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             kern<<<1, 32 * WPB, smem, s>>>(A, 0);

@@ -520,9 +520,24 @@ hh_status hh_matvec_backward(hh_ctx* ctx, const hh_hmat* h, const double* gU_dev
                              double* gX_dev, float* gtheta_dev, void* stream)
 {
     if (!ctx || !h) return HH_ERR_ARG;
+    if (gF_dev) {
+        // dL/dF = alpha_1 gU + M_H^T gU: the transposed product
+        hh_status st = hh_matvec(ctx, h, gU_dev, gF_dev, 1, stream);
+        if (st != HH_OK) return st;
+    }
+    if (!gX_dev && !gtheta_dev) return HH_OK;
     return guarded(ctx, [&]() -> hh_status {
-        (void)gU_dev; (void)F_dev; (void)gF_dev; (void)gX_dev; (void)gtheta_dev; (void)stream;
-        throw HHError{HH_ERR_ARG, "hh_matvec_backward is not available in this build"};
+        HH_REQUIRE(gU_dev && F_dev, HH_ERR_ARG, "gU or F is NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        const hh_tree* t = h->tree;
+        double* Fs = dev_alloc_t<double>(3 * t->n, s);
+        double* Ws = dev_alloc_t<double>(3 * t->n, s);
+        gather_rows(F_dev, t->perm, t->n, Fs, s);
+        gather_rows(gU_dev, t->perm, t->n, Ws, s);
+        matvec_backward_xtheta(ctx, h, Fs, Ws, gX_dev, gtheta_dev, s);
+        dev_free(Fs, s);
+        dev_free(Ws, s);
+        return HH_OK;
     });
 }
 

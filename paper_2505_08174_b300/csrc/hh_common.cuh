@@ -113,14 +113,17 @@ template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return 
 // FP32 (the fast SIMT path) reads a transposed copy of the parameters kept in
 // shared memory: W1t [4][W], b1, W2t [W][W], b2, W3t [W][W], b3, W4t [W][8]
 // (6 outputs padded to 8), b4 [8]; every row starts on a 16-byte boundary so
-// weights come in as float4.  Input-major order keeps the W accumulators in
-// registers.  The empty asm with a memory clobber stops the compiler from
-// hoisting all weight loads out of the caller's pair loop (which would spill).
+// weights come in as float4.  A layer's W outputs accumulate in registers;
+// its input vector sits in this thread's column of a per-warp shared buffer
+// (hs[32 * i], one column per lane: conflict-free), so the input loop stays
+// rolled and the whole network is ~900 instructions -- small enough for the
+// instruction cache of the large ACA kernels.  The empty asm with a memory
+// clobber keeps the weight loads inside the caller's pair loop.
 template <int W>
 __host__ __device__ constexpr int mlp_t_size() { return 4 * W + W + W * W + W + W * W + W + 8 * W + 8; }
 
 template <int W>
-__device__ __forceinline__ void mlp_f32(const float* __restrict__ th, const float* f, float* o)
+__device__ __forceinline__ void mlp_f32(const float* __restrict__ th, const float* f, float* o, float* hs)
 {
     asm volatile("" ::: "memory");
     const float* W1 = th;
@@ -131,31 +134,29 @@ __device__ __forceinline__ void mlp_f32(const float* __restrict__ th, const floa
     const float* b3 = W3 + W * W;
     const float* W4 = b3 + W;
     const float* b4 = W4 + 8 * W;
-    float h[W], g[W];
+    float g[W];
 #pragma unroll
-    for (int j = 0; j < W; ++j) h[j] = b1[j];
+    for (int j = 0; j < W; ++j) g[j] = b1[j];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const float x = f[i];
 #pragma unroll
         for (int j = 0; j < W; j += 4) {
             const float4 w4 = *reinterpret_cast<const float4*>(W1 + i * W + j);
-            h[j] += w4.x * x; h[j + 1] += w4.y * x; h[j + 2] += w4.z * x; h[j + 3] += w4.w * x;
+            g[j] += w4.x * x; g[j + 1] += w4.y * x; g[j + 2] += w4.z * x; g[j + 3] += w4.w * x;
         }
     }
 #pragma unroll
-    for (int j = 0; j < W; ++j) h[j] = silu_f(h[j]);
-    // layers 2 and 3 share one (looped) body: half the code, which matters
-    // for the instruction cache of the large ACA kernels
+    for (int j = 0; j < W; ++j) hs[32 * j] = silu_f(g[j]);
 #pragma unroll 1
     for (int l = 0; l < 2; ++l) {
         const float* Wl = l == 0 ? W2 : W3;
         const float* bl = l == 0 ? b2 : b3;
 #pragma unroll
         for (int j = 0; j < W; ++j) g[j] = bl[j];
-#pragma unroll
+#pragma unroll 2
         for (int i = 0; i < W; ++i) {
-            const float x = h[i];
+            const float x = hs[32 * i];
 #pragma unroll
             for (int j = 0; j < W; j += 4) {
                 const float4 w4 = *reinterpret_cast<const float4*>(Wl + i * W + j);
@@ -163,12 +164,12 @@ __device__ __forceinline__ void mlp_f32(const float* __restrict__ th, const floa
             }
         }
 #pragma unroll
-        for (int j = 0; j < W; ++j) h[j] = silu_f(g[j]);
+        for (int j = 0; j < W; ++j) hs[32 * j] = silu_f(g[j]);
     }
     float oo[6] = {b4[0], b4[1], b4[2], b4[3], b4[4], b4[5]};
-#pragma unroll
+#pragma unroll 4
     for (int i = 0; i < W; ++i) {
-        const float x = h[i];
+        const float x = hs[32 * i];
         const float4 a = *reinterpret_cast<const float4*>(W4 + i * 8);
         const float2 c = *reinterpret_cast<const float2*>(W4 + i * 8 + 4);
         oo[0] += a.x * x; oo[1] += a.y * x; oo[2] += a.z * x; oo[3] += a.w * x; oo[4] += c.x * x; oo[5] += c.y * x;
@@ -176,6 +177,10 @@ __device__ __forceinline__ void mlp_f32(const float* __restrict__ th, const floa
 #pragma unroll
     for (int j = 0; j < 6; ++j) o[j] = oo[j];
 }
+
+// Floats of per-warp activation buffer a SIMT kernel of (R, KIND) needs.
+template <typename R, int KIND>
+__host__ __device__ constexpr int act_floats_per_warp() { return (sizeof(R) == 4 && KIND < 2) ? (KIND == 1 ? 64 : 32) * 32 : 0; }
 
 // FP64 (the parity mode) reads the packed layout (W [out,in] row-major, then
 // b) with compact loops; one out-of-line copy per width.
@@ -222,9 +227,9 @@ __device__ __noinline__ void mlp_f64(const double* __restrict__ th, const double
 }
 
 template <typename R, int W>
-__device__ __forceinline__ void mlp_simt(const R* __restrict__ th, const R* f, R* o)
+__device__ __forceinline__ void mlp_simt(const R* __restrict__ th, const R* f, R* o, R* hs)
 {
-    if constexpr (sizeof(R) == 4) mlp_f32<W>(th, f, o);
+    if constexpr (sizeof(R) == 4) mlp_f32<W>(th, f, o, hs);
     else mlp_f64<W>(th, f, o);
 }
 
@@ -232,9 +237,11 @@ struct PairParams {
     double a, mu;
 };
 
-// KIND 0 = MLP width 32, 1 = MLP width 64, 2 = RPY.
+// KIND 0 = MLP width 32, 1 = MLP width 64, 2 = RPY.  hs: this thread's
+// column of the per-warp activation buffer (FP32 MLP only; see mlp_f32).
 template <typename R, int KIND>
-__device__ __forceinline__ void pair_block(const R* __restrict__ th, const PairParams& pp, R rx, R ry, R rz, R K[9])
+__device__ __forceinline__ void pair_block(const R* __restrict__ th, const PairParams& pp, R rx, R ry, R rz, R K[9],
+                                           R* hs)
 {
     R d2 = rx * rx + ry * ry + rz * rz;
     R id = rsqrt_<R>(d2);
@@ -258,7 +265,7 @@ __device__ __forceinline__ void pair_block(const R* __restrict__ th, const PairP
     } else {
         R f[4] = {rx * id, ry * id, rz * id, (R)pp.a * id};
         R o[6];
-        mlp_simt<R, (KIND == 0 ? 32 : 64)>(th, f, o);
+        mlp_simt<R, (KIND == 0 ? 32 : 64)>(th, f, o, hs);
         K[0] = o[0] * id; K[1] = o[3] * id; K[2] = o[4] * id;
         K[3] = o[3] * id; K[4] = o[1] * id; K[5] = o[5] * id;
         K[6] = o[4] * id; K[7] = o[5] * id; K[8] = o[2] * id;

@@ -132,6 +132,11 @@ void eval_pairs_tc(hh_ctx* ctx, const double* r, int64_t n, double a, double* K,
 // SIMT K(r) for a list of separations (hh_near.cu), FP32 or FP64 per p.
 void eval_pairs_simt(hh_ctx* ctx, const hh_params& p, const double* r, int64_t n, double* K, cudaStream_t s);
 
+// Adjoint: dL/dX (added to gX, caller order) and dL/dtheta (added to gtheta)
+// of L = sum w . (M_H F) with frozen pivots (hh_backward.cu); Fs, Ws sorted.
+void matvec_backward_xtheta(hh_ctx* ctx, const hh_hmat* h, const double* Fs, const double* Ws, double* gX,
+                            float* gtheta, cudaStream_t s);
+
 // Training of the pair MLP (hh_train.cu).
 double train_loss_grad(hh_ctx* ctx, const float* theta, int width, const double* r, const double* e, const double* U,
                        int64_t B, double a, float* grad_dev, cudaStream_t s);

@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(32 * NEAR_WPB) k_near(const double* __restrict
     for (int i = threadIdx.x; i < n_th; i += blockDim.x) th[i] = th_g[i];
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    R* hs = th + n_th + (threadIdx.x >> 5) * act_floats_per_warp<R, KIND>() + lane;
     const int64_t wid = (int64_t)blockIdx.x * NEAR_WPB + (threadIdx.x >> 5);
     const int64_t nwarps = (int64_t)gridDim.x * NEAR_WPB;
     for (int64_t w = wid; w < n_work; w += nwarps) {
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(32 * NEAR_WPB) k_near(const double* __restrict
                     R rx, ry, rz, K[9];
                     if (!transpose) sep<R>(Xs, gm, gn, rx, ry, rz);
                     else sep<R>(Xs, gn, gm, rx, ry, rz);
-                    pair_block<R, KIND>(th, pp, rx, ry, rz, K);
+                    pair_block<R, KIND>(th, pp, rx, ry, rz, K, hs);
                     acc[i][0] += K[0] * f0 + K[1] * f1 + K[2] * f2;
                     acc[i][1] += K[3] * f0 + K[4] * f1 + K[5] * f2;
                     acc[i][2] += K[6] * f0 + K[7] * f1 + K[8] * f2;
@@ -114,7 +115,7 @@ void launch_near(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_par
 {
     int n_th = 0;
     const R* th = theta_for<R>(ctx, p, &n_th);
-    const size_t smem = sizeof(R) * (size_t)n_th;
+    const size_t smem = sizeof(R) * ((size_t)n_th + act_floats_per_warp<R, KIND>() * NEAR_WPB);
     HH_CUDA(cudaFuncSetAttribute(k_near<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t blocks = std::min<int64_t>(ceil_div(n_work, NEAR_WPB), (int64_t)ctx->n_sm * 16);
     HH_CUDA(cudaEventRecord(ctx->kev[4], s));
@@ -229,9 +230,10 @@ __global__ void k_eval_pairs(const double* __restrict__ r, int64_t n, const R* _
     R* th = reinterpret_cast<R*>(smem_raw);
     for (int i = threadIdx.x; i < n_th; i += blockDim.x) th[i] = th_g[i];
     __syncthreads();
+    R* hs = th + n_th + (threadIdx.x >> 5) * act_floats_per_warp<R, KIND>() + (threadIdx.x & 31);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         R k[9];
-        pair_block<R, KIND>(th, pp, (R)r[3 * i], (R)r[3 * i + 1], (R)r[3 * i + 2], k);
+        pair_block<R, KIND>(th, pp, (R)r[3 * i], (R)r[3 * i + 1], (R)r[3 * i + 2], k, hs);
 #pragma unroll
         for (int e = 0; e < 9; ++e) K[9 * i + e] = (double)k[e];
     }
@@ -242,7 +244,7 @@ void launch_eval(hh_ctx* ctx, const hh_params& p, const double* r, int64_t n, do
 {
     int n_th = 0;
     const R* th = theta_for<R>(ctx, p, &n_th);
-    const size_t smem = sizeof(R) * (size_t)n_th;
+    const size_t smem = sizeof(R) * ((size_t)n_th + act_floats_per_warp<R, KIND>() * 4);
     HH_CUDA(cudaFuncSetAttribute(k_eval_pairs<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t blocks = std::min<int64_t>(ceil_div(n, 128), (int64_t)ctx->n_sm * 8);
     k_eval_pairs<R, KIND><<<(unsigned)blocks, 128, smem, s>>>(r, n, th, n_th, PairParams{p.radius, p.viscosity}, K);
