@@ -7,8 +7,10 @@ admissibility partition, batched ACA fused with the low-rank apply, dense
 inadmissible blocks, FP64 accumulation.  Workload: N = 1,000,000 spheres
 (a = 1) placed by random sequential addition in a cube at volume fraction
 0.1, forces N(0,1), pair MLP 4->32->32->32->6 (SiLU, Xavier weights rounded to
-bf16), C_leaf = 32, eta = 1, zeta = 1e-4, max_rank 48, FP32 kernels with FP64
-pivots / norms / accumulation.
+bf16), C_leaf = 64, eta = 1, zeta = 1e-4, max_rank 48.  Precision "bf16"
+(default): near-field MLP on tcgen05 tensor cores with BF16 operands and FP32
+accumulation, ACA and low-rank apply in FP32, FP64 pivot inverses, norms and
+final accumulation; "fp32" and "fp64" run every kernel in that type.
 
 value    = N * K / (sum of CUDA-event times of the K predictions), inputs
            resident in HBM; L2 (126 MB) is flushed between steps by writing a
@@ -44,6 +46,12 @@ sys.path.insert(0, ROOT)
 FLOP_PER_QUERY = {32: 2 * (4 * 32 + 32 * 32 + 32 * 32 + 32 * 6) + 4 * 96 + 25,
                   64: 2 * (4 * 64 + 64 * 64 + 64 * 64 + 64 * 6) + 4 * 192 + 25}
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+PRECISION_NOTE = {
+    "bf16": "near-field MLP BF16 operands / FP32 accumulate on tcgen05; ACA + low-rank apply FP32; FP64 pivots, "
+            "norms and final sum",
+    "fp32": "all kernels FP32; FP64 pivots, norms and final sum",
+    "fp64": "all kernels FP64",
+}
 METRIC = "particle-velocities/sec per H-HIGNN prediction at N=1M; rel. L2 err vs FP64 dense"
 
 
@@ -230,9 +238,10 @@ def run_ours(args, rank, world):
     line = {
         "metric": METRIC, "value": value, "unit": "particle-velocities/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else prec, "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16"}[prec], "data": "synthetic",
         "config": {"workload": f"uniform_cube_rsa_N{n}_phi0.1_mlp4-32-32-32-6", "n": n, "leaf_size": args.leaf,
                    "eta": 1.0, "eps": args.eps, "max_rank": 48, "precision": prec,
+                   "arithmetic": PRECISION_NOTE[prec],
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"independent suspension per GPU"},
         "rel_err": rel_err, "rel_err_rows": len(idx),
         "stages_ms": {k: st[k] for k in ("t_tree", "t_part", "t_near", "t_aca", "t_acc")},
@@ -262,8 +271,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--eps", type=float, default=1e-4)
-    ap.add_argument("--leaf", type=int, default=32)
-    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=2)

@@ -542,7 +542,7 @@ __global__ void k_max_dim(const int32_t* __restrict__ work, int64_t n, const int
 
 template <typename R, int KIND>
 void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_small, const int32_t* work_large,
-                int64_t n_large, int max_large_cq, int mode, cudaStream_t s)
+                int64_t n_large, int max_small_cq, int max_large_cq, int mode, cudaStream_t s)
 {
     const int th_bytes = A.n_th * (int)sizeof(R);
     const int mr = std::min(A.max_rank, MAXR);
@@ -573,7 +573,9 @@ void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_
     if (n_small > 0) {
         int64_t blocks = std::min<int64_t>(ceil_div(n_small, WPB), 4 * ctx->n_sm);
         int64_t teams = blocks * WPB;
-        int64_t stride = (int64_t)2 * SMALL_MAX * 9 * mr;
+        // factors (max_rank x 9 x (c+q) reals), rounded to 256 B
+        int64_t stride = (int64_t)std::min(max_small_cq, 2 * SMALL_MAX) * 9 * mr;
+        stride = ceil_div(stride * (int64_t)sizeof(R), 256) * 256 / (int64_t)sizeof(R);
         R* scratch = dev_alloc_t<R>(stride * teams, s);
         HH_CUDA(cudaMemsetAsync(A.counter + 1, 0, sizeof(unsigned long long), s));
         AcaArgs<R> B = A;
@@ -708,7 +710,6 @@ void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_para
     int32_t* wl = dev_alloc_t<int32_t>(h[1], s);
     k_compact<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(fs, os, nG, ws);
     HH_CHECK_LAUNCH();
-    int max_cq = 0;
     if (h[1] > 0) {
         uint64_t* lk = dev_alloc_t<uint64_t>(h[1], s);
         k_compact_keys<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(fl, ol, key, nG, lk);
@@ -717,18 +718,30 @@ void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_para
         k_keys_to_work<<<(unsigned)ceil_div(h[1], 256), 256, 0, s>>>(lk, h[1], wl);
         HH_CHECK_LAUNCH();
         dev_free(lk, s);
-        int* dmax = dev_alloc_t<int>(1, s);
-        HH_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), s));
-        k_max_dim<<<(unsigned)ceil_div(h[1], 256), 256, 0, s>>>(wl, h[1], bl->PG, t->nbeg, t->nend, dmax);
-        HH_CHECK_LAUNCH();
-        HH_CUDA(cudaMemcpyAsync(&max_cq, dmax, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+    // largest c + q of each list: sizes the per-team factor workspaces
+    int dims[2] = {0, 0};
+    if (h[0] + h[1] > 0) {
+        int* dmax = dev_alloc_t<int>(2, s);
+        HH_CUDA(cudaMemsetAsync(dmax, 0, 2 * sizeof(int), s));
+        if (h[0] > 0) {
+            k_max_dim<<<(unsigned)ceil_div(h[0], 256), 256, 0, s>>>(ws, h[0], bl->PG, t->nbeg, t->nend, dmax);
+            HH_CHECK_LAUNCH();
+        }
+        if (h[1] > 0) {
+            k_max_dim<<<(unsigned)ceil_div(h[1], 256), 256, 0, s>>>(wl, h[1], bl->PG, t->nbeg, t->nend, dmax + 1);
+            HH_CHECK_LAUNCH();
+        }
+        HH_CUDA(cudaMemcpyAsync(dims, dmax, sizeof dims, cudaMemcpyDeviceToHost, s));
         HH_CUDA(cudaStreamSynchronize(s));
         dev_free(dmax, s);
     }
+    const int max_cq = dims[1];
+    const int max_small_cq = dims[0];
     const int kind = kernel_kind(p, ctx->width);
-    if (kind == 0) launch_aca<R, 0>(ctx, A, ws, h[0], wl, h[1], max_cq, r.mode, s);
-    else if (kind == 1) launch_aca<R, 1>(ctx, A, ws, h[0], wl, h[1], max_cq, r.mode, s);
-    else launch_aca<R, 2>(ctx, A, ws, h[0], wl, h[1], max_cq, r.mode, s);
+    if (kind == 0) launch_aca<R, 0>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, r.mode, s);
+    else if (kind == 1) launch_aca<R, 1>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, r.mode, s);
+    else launch_aca<R, 2>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, r.mode, s);
     dev_free(fs, s); dev_free(fl, s); dev_free(os, s); dev_free(ol, s); dev_free(key, s); dev_free(tot, s);
     dev_free(ws, s); dev_free(wl, s);
 }
@@ -768,7 +781,7 @@ void aca_single_block_ws(hh_ctx* ctx, const hh_params& p, int32_t c, int32_t q, 
                          unsigned long long* counter, void* ws, void* part, const int64_t* pofs, int32_t* rank,
                          cudaStream_t s)
 {
-    HH_REQUIRE(c >= 1 && q >= 1 && c <= SMALL_MAX && q <= SMALL_MAX, HH_ERR_ARG, "block sides must be in [1, 128]");
+    HH_REQUIRE(c >= 1 && q >= 1 && c <= SMALL_MAX && q <= SMALL_MAX, HH_ERR_ARG, "block sides must be in [1, 512]");
     auto go = [&](auto tag) {
         using R = decltype(tag);
         AcaArgs<R> A{};
