@@ -187,9 +187,14 @@ hh_status hh_aca_block_apply_noalloc(hh_ctx *ctx, const double *Xt_dev, int32_t 
                                      int32_t *rank_dev);
 
 /* Adjoint of L = sum_i gU_i . U_i for U = alpha_1 F + M_H F built by hh_aca
- * with the MLP kernel: gF_dev = alpha_1 gU + M_H^T gU (FP64 [N,3]),
- * gX_dev += dL/dX (FP64 [N,3]) and gtheta_dev += dL/dtheta (float32, length
- * of theta), the last two with tree, partition and pivots frozen.  Any of
+ * with the MLP kernel (Section 3, Eqs. 4 and 8 differentiated; the paper
+ * trains the MLP on pairs and has no H-matrix adjoint): gF_dev = alpha_1 gU
+ * + M_H^T gU (FP64 [N,3]), gX_dev += dL/dX (FP64 [N,3]) and gtheta_dev +=
+ * dL/dtheta (float32, length of theta), the last two with tree, partition
+ * and ACA pivots frozen, evaluated in FP64.  For an FP32 or BF16 h, dL/dX and
+ * dL/dtheta are those of the FP64 H-matrix on the same tree and partition
+ * (its ACA is run inside the call): pivots picked from low-precision
+ * residuals do not give a usable derivative of the rank recursion.  Any of
  * gF_dev, gX_dev, gtheta_dev may be NULL; gX and gtheta are accumulated
  * into (zero them first).  Near-field activations are recomputed, not
  * stored. */

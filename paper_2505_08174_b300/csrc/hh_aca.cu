@@ -26,203 +26,13 @@
 // the cross term and the lambda^2 recurrence are reduced and kept in FP64.
 #include <algorithm>
 
-#include "hh_internal.h"
+#include "hh_aca.cuh"
 
 namespace {
 
-constexpr int MAXR = 64;          // hard cap on max_rank
-constexpr int WARP_ROWS = 16;     // warp team: up to 512 rows / columns per block
-constexpr int CTA_T = 256;        // CTA team size
-constexpr int SMALL_MAX = 32 * WARP_ROWS;
-
-template <typename R>
-struct AcaArgs {
-    const double* Xs;
-    const R* th_g;   // parameters in global memory (copied to shared)
-    int n_th;
-    PairParams pp;
-    const double* Fs;
-    const int32_t* PG;
-    const int32_t* nbeg;
-    const int32_t* nend;
-    const int32_t* work;
-    int64_t n_work;
-    unsigned long long* counter;
-    int max_rank;
-    double eps2;
-    int j1_rule;
-    uint64_t seed;
-    R* scratch;
-    int64_t team_stride;   // reals per team
-    int32_t* rank;
-    int32_t* pivI;
-    int32_t* pivJ;
-    R* part;
-    const int64_t* pofs;
-    R* fac;
-    const int64_t* fofs;
-    unsigned* status;
-    unsigned long long* n_queries;
-};
-
-template <typename R>
-struct alignas(16) TeamSmem {
-    R qj[MAXR * 9];        // Q_p(j_k), p < k
-    R ci[MAXR * 9];        // C_p(i_k), p < k
-    R A[(MAXR + 1) * 9];   // A_pk, p <= k
-    double red[2][8];      // per-warp partials of nu^2 and the cross term
-    R Pi[9];
-    R tv[MAXR * 3];
-    double rv[8];
-    int ri[8];
-    int flag, stop;
-};
-
-__device__ __forceinline__ uint64_t splitmix_once(uint64_t x)
-{
-    uint64_t z = x + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-// j_1 (drawn at random in the paper): rule 0 = first source, rule 1 =
-// splitmix64(seed ^ (t << 32) ^ s) mod q.
-__device__ __forceinline__ int j1_of(int rule, uint64_t seed, int t, int s, int q)
-{
-    if (rule == 0 || q <= 1) return 0;
-    uint64_t h = splitmix_once(seed ^ ((uint64_t)(uint32_t)t << 32) ^ (uint64_t)(uint32_t)s);
-    return (int)(h % (uint64_t)q);
-}
-
-// ---- teams -----------------------------------------------------------------
-struct WarpTeam {
-    static constexpr int SIZE = 32;
-    static constexpr int ROWS = WARP_ROWS;   // rows per thread
-    static constexpr int NW = 1;
-    static constexpr bool REG_FLAGS = true;  // used-row/column flags in registers
-    __device__ __forceinline__ int tid() const { return threadIdx.x & 31; }
-    __device__ __forceinline__ int warp() const { return 0; }
-    __device__ __forceinline__ void sync() const { __syncwarp(); }
-    template <typename T, typename S>
-    __device__ __forceinline__ void argmax(T& v, int& i, S&) const { warp_argmax(v, i); }
-};
-
-struct CtaTeam {
-    static constexpr int SIZE = CTA_T;
-    static constexpr int ROWS = 1 << 20;      // unbounded (loops exit at c / q)
-    static constexpr int NW = CTA_T / 32;
-    static constexpr bool REG_FLAGS = false;  // flags as bytes in the team workspace
-    __device__ __forceinline__ int tid() const { return threadIdx.x; }
-    __device__ __forceinline__ int warp() const { return threadIdx.x >> 5; }
-    __device__ __forceinline__ void sync() const { __syncthreads(); }
-    template <typename T, typename S>
-    __device__ __forceinline__ void argmax(T& v, int& i, S& sm) const
-    {
-        warp_argmax(v, i);
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        __syncthreads();
-        if (lane == 0) { sm.rv[w] = (double)v; sm.ri[w] = i; }
-        __syncthreads();
-        double bv = sm.rv[0];
-        int bi = sm.ri[0];
-        for (int k = 1; k < NW; ++k) {
-            double ov = sm.rv[k];
-            int oi = sm.ri[k];
-            if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
-        }
-        v = (T)bv;
-        i = bi;
-        __syncthreads();
-    }
-};
-
-template <typename R>
-__device__ __forceinline__ void ld9(const R* __restrict__ base, int64_t stride, int64_t idx, R* v)
-{
-#pragma unroll
-    for (int e = 0; e < 9; ++e) v[e] = base[e * stride + idx];
-}
-template <typename R>
-__device__ __forceinline__ void st9(R* __restrict__ base, int64_t stride, int64_t idx, const R* v)
-{
-#pragma unroll
-    for (int e = 0; e < 9; ++e) base[e * stride + idx] = v[e];
-}
-
-// sm.A[p] = sum_x C_p(x)^T C_k(x) for p = 0..k (each warp of the team owns a
-// subset of p and sweeps all rows with its 32 lanes).
-template <typename R, class Team>
-__device__ void gram_cols(const Team& tm, TeamSmem<R>& sm, const R* Cs, int c, int k)
-{
-    const int lane = threadIdx.x & 31;
-    const R* Ck = Cs + (int64_t)k * 9 * c;
-    for (int p = tm.warp(); p <= k; p += Team::NW) {
-        const R* Cp = Cs + (int64_t)p * 9 * c;
-        R acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int x = lane; x < c; x += 32) {
-            R a[9], b[9];
-            ld9(Cp, c, x, a);
-            ld9(Ck, c, x, b);
-#pragma unroll
-            for (int u = 0; u < 3; ++u)
-#pragma unroll
-                for (int v = 0; v < 3; ++v) acc[3 * u + v] += a[u] * b[v] + a[3 + u] * b[3 + v] + a[6 + u] * b[6 + v];
-        }
-#pragma unroll
-        for (int e = 0; e < 9; ++e) {
-            R s = warp_sum(acc[e]);
-            if (lane == 0) sm.A[9 * p + e] = s;
-        }
-    }
-}
-
-// nu^2 = tr(A_kk B_kk) and cross = sum_{p<k} tr(A_pk B_kp), B_kp = sum_n q_k(n) q_p(n)^T.
-// tr(A B) is linear in B, so each thread adds
-//   tr(A_pk q_k(n) q_p(n)^T) = <A_pk q_k(n), q_p(n)>_F
-// over its own columns n and only two scalars are reduced across the team.
-// Thread 0 receives the sums (FP64).
-template <typename R, class Team>
-__device__ void gram_rows(const Team& tm, TeamSmem<R>& sm, const R* Qs, int q, int k, double& nu2, double& cross)
-{
-    constexpr int SIZE = Team::SIZE;
-    const int tid = tm.tid(), lane = threadIdx.x & 31;
-    const R* Qk = Qs + (int64_t)k * 9 * q;
-    R snu = 0, scr = 0;
-    for (int n = tid; n < q; n += SIZE) {
-        R qk[9];
-        ld9(Qk, q, n, qk);
-        for (int p = 0; p <= k; ++p) {
-            R qp[9], T[9];
-            if (p == k) {
-#pragma unroll
-                for (int e = 0; e < 9; ++e) qp[e] = qk[e];
-            } else {
-                ld9(Qs + (int64_t)p * 9 * q, q, n, qp);
-            }
-            mm3(sm.A + 9 * p, qk, T);
-            R d = 0;
-#pragma unroll
-            for (int e = 0; e < 9; ++e) d += T[e] * qp[e];
-            if (p == k) snu += d; else scr += d;
-        }
-    }
-    double a = warp_sum((double)snu), b = warp_sum((double)scr);
-    if constexpr (Team::NW > 1) {
-        if (lane == 0) { sm.red[0][tm.warp()] = a; sm.red[1][tm.warp()] = b; }
-        tm.sync();
-        if (tid == 0) {
-            a = 0.0; b = 0.0;
-            for (int w = 0; w < Team::NW; ++w) { a += sm.red[0][w]; b += sm.red[1][w]; }
-        }
-    }
-    nu2 = a;
-    cross = b;
-}
-
 // ---- the per-block ACA -----------------------------------------------------
-template <typename R, int KIND, class Team>
-__device__ void aca_block(const AcaArgs<R>& A, const Team& tm, TeamSmem<R>& sm, const R* th, R* hs, R* Cs_base,
+template <typename R, int KIND, class Team, class S>
+__device__ void aca_block(const AcaArgs<R>& A, const Team& tm, S& sm, const R* th, R* hs, R* Cs_base,
                           int64_t b, int mode)
 {
     constexpr int ROWS = Team::ROWS, SIZE = Team::SIZE;
@@ -668,28 +478,7 @@ void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_para
     const int64_t nG = bl->nG;
     if (nG == 0) return;
     HH_REQUIRE(p.max_rank >= 1 && p.max_rank <= MAXR, HH_ERR_ARG, "max_rank must be in [1, 64]");
-    AcaArgs<R> A{};
-    A.Xs = t->Xs;
-    A.th_g = theta_for<R>(ctx, p, &A.n_th);
-    A.pp = PairParams{p.radius, p.viscosity};
-    A.Fs = r.Fs;
-    A.PG = bl->PG;
-    A.nbeg = t->nbeg;
-    A.nend = t->nend;
-    A.counter = ctx->d_counters;
-    A.max_rank = p.max_rank;
-    A.eps2 = p.eps * p.eps;
-    A.j1_rule = p.j1_rule;
-    A.seed = p.seed;
-    A.rank = r.rank;
-    A.pivI = r.pivI;
-    A.pivJ = r.pivJ;
-    A.part = (R*)r.part;
-    A.pofs = r.pofs;
-    A.fac = (R*)r.factors;
-    A.fofs = r.fofs;
-    A.status = ctx->d_status;
-    A.n_queries = ctx->d_counters + 4;
+    AcaArgs<R> A = make_aca_args<R>(ctx, t, bl, p, r);
 
     // work lists: small blocks in block order, large blocks by decreasing c + q
     int64_t* fs = dev_alloc_t<int64_t>(nG, s);
@@ -739,6 +528,14 @@ void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_para
     const int max_cq = dims[1];
     const int max_small_cq = dims[0];
     const int kind = kernel_kind(p, ctx->width);
+    if constexpr (sizeof(R) == 4) {
+        if (p.precision == HH_BF16 && kind < 2) {
+            aca_tc_run(ctx, t, bl, p, r, ws, h[0], wl, h[1], max_small_cq, max_cq, s);
+            dev_free(fs, s); dev_free(fl, s); dev_free(os, s); dev_free(ol, s); dev_free(key, s); dev_free(tot, s);
+            dev_free(ws, s); dev_free(wl, s);
+            return;
+        }
+    }
     if (kind == 0) launch_aca<R, 0>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, r.mode, s);
     else if (kind == 1) launch_aca<R, 1>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, r.mode, s);
     else launch_aca<R, 2>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, r.mode, s);

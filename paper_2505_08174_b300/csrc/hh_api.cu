@@ -526,19 +526,31 @@ hh_status hh_matvec_backward(hh_ctx* ctx, const hh_hmat* h, const double* gU_dev
         if (st != HH_OK) return st;
     }
     if (!gX_dev && !gtheta_dev) return HH_OK;
-    return guarded(ctx, [&]() -> hh_status {
+    // dL/dX and dL/dtheta differentiate the FP64 rank recursion: a narrower
+    // H-matrix is re-approximated in FP64 on the same tree and partition
+    hh_hmat* h64 = nullptr;
+    if (h->real_bytes != 8) {
+        hh_params p64 = h->params;
+        p64.precision = HH_FP64;
+        hh_status st = hh_aca(ctx, h->tree, h->blocks, &p64, stream, &h64);
+        if (st != HH_OK) return st;
+    }
+    const hh_hmat* hx = h64 ? h64 : h;
+    hh_status st = guarded(ctx, [&]() -> hh_status {
         HH_REQUIRE(gU_dev && F_dev, HH_ERR_ARG, "gU or F is NULL");
         cudaStream_t s = (cudaStream_t)stream;
-        const hh_tree* t = h->tree;
+        const hh_tree* t = hx->tree;
         double* Fs = dev_alloc_t<double>(3 * t->n, s);
         double* Ws = dev_alloc_t<double>(3 * t->n, s);
         gather_rows(F_dev, t->perm, t->n, Fs, s);
         gather_rows(gU_dev, t->perm, t->n, Ws, s);
-        matvec_backward_xtheta(ctx, h, Fs, Ws, gX_dev, gtheta_dev, s);
+        matvec_backward_xtheta(ctx, hx, Fs, Ws, gX_dev, gtheta_dev, s);
         dev_free(Fs, s);
         dev_free(Ws, s);
         return HH_OK;
     });
+    if (h64) hh_hmat_free(h64);
+    return st;
 }
 
 hh_status hh_export_tree(const hh_tree* t, int32_t* perm, uint64_t* codes, int32_t* node_begin, int32_t* node_end,

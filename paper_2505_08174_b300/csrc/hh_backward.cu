@@ -339,73 +339,14 @@ __device__ __forceinline__ void st9g(R* base, int64_t ld, int64_t x, const R* v)
     for (int e = 0; e < 9; ++e) base[e * ld + x] = v[e];
 }
 
-// Factors of one admissible block recomputed in R along the frozen pivots
-// (the forward ran in a narrower precision): the same recursion as the
-// forward rank loop, without the pivot search.  C [l][9][c] then Q [l][9][q].
-template <typename R, int W>
-__device__ void refactor(const R* th, R a, const double* __restrict__ Xs, int32_t t0, int32_t c, int32_t s0,
-                         int32_t q, const int32_t* I, const int32_t* J, int l, R* C, R* Pi)
-{
-    const int lane = threadIdx.x & 31;
-    R* Q = C + (int64_t)l * 9 * c;
-    for (int k = 0; k < l; ++k) {
-        const int ik = I[k], jk = J[k];
-        R* Ck = C + (int64_t)k * 9 * c;
-        R* Qk = Q + (int64_t)k * 9 * q;
-        for (int m = lane; m < c; m += 32) {
-            R rx, ry, rz, K[9];
-            sep<R>(Xs, t0 + m, s0 + jk, rx, ry, rz);
-            entry_forward<R, W>(th, a, rx, ry, rz, K);
-            for (int p = 0; p < k; ++p) {
-                R cp[9], qp[9], t9[9];
-                ld9g(C + (int64_t)p * 9 * c, c, m, cp);
-                ld9g(Q + (int64_t)p * 9 * q, q, jk, qp);
-                mm3(cp, qp, t9);
-                for (int e = 0; e < 9; ++e) K[e] -= t9[e];
-            }
-            st9g(Ck, c, m, K);
-        }
-        __syncwarp();
-        if (lane == 0) {
-            double P[9], Pd[9];
-            for (int e = 0; e < 9; ++e) P[e] = (double)Ck[(int64_t)e * c + ik];
-            inv3d(P, Pd);
-            for (int e = 0; e < 9; ++e) Pi[e] = (R)Pd[e];
-        }
-        __syncwarp();
-        for (int m = lane; m < c; m += 32) {
-            R v[9], o[9];
-            ld9g(Ck, c, m, v);
-            mm3(v, Pi, o);
-            st9g(Ck, c, m, o);
-        }
-        __syncwarp();
-        for (int n = lane; n < q; n += 32) {
-            R rx, ry, rz, K[9];
-            sep<R>(Xs, t0 + ik, s0 + n, rx, ry, rz);
-            entry_forward<R, W>(th, a, rx, ry, rz, K);
-            for (int p = 0; p < k; ++p) {
-                R cp[9], qp[9], t9[9];
-                ld9g(C + (int64_t)p * 9 * c, c, ik, cp);
-                ld9g(Q + (int64_t)p * 9 * q, q, n, qp);
-                mm3(cp, qp, t9);
-                for (int e = 0; e < 9; ++e) K[e] -= t9[e];
-            }
-            st9g(Qk, q, n, K);
-        }
-        __syncwarp();
-    }
-}
-
 template <typename R, int W>
 __global__ void __launch_bounds__(32) k_far_bwd(const double* __restrict__ Xs, const double* __restrict__ Fs,
                                                 const double* __restrict__ Ws, const int32_t* __restrict__ PG,
                                                 int64_t nG, const int32_t* __restrict__ nbeg,
                                                 const int32_t* __restrict__ nend, const int32_t* __restrict__ rank,
                                                 const int32_t* __restrict__ pivI, const int32_t* __restrict__ pivJ,
-                                                int max_rank, int shard, int n_shards, const void* __restrict__ fac,
-                                                int fac_bytes, const int64_t* __restrict__ fofs,
-                                                const R* __restrict__ th_g, R a,
+                                                int max_rank, int shard, int n_shards, const R* __restrict__ fac,
+                                                const int64_t* __restrict__ fofs, const R* __restrict__ th_g, R a,
                                                 R* __restrict__ scratch, int64_t ws_stride,
                                                 const int32_t* __restrict__ perm, double* gX, double* gth, R* gacc)
 {
@@ -415,7 +356,6 @@ __global__ void __launch_bounds__(32) k_far_bwd(const double* __restrict__ Xs, c
     bwd_setup<R, W>(sm, th_g, gacc);
     const int lane = threadIdx.x & 31;
     R* Cb = scratch + (int64_t)blockIdx.x * ws_stride;
-    R* Cw = Cb + ws_stride / 2;   // factors recomputed in R when the stored ones are narrower
     for (int64_t b = blockIdx.x; b < nG; b += gridDim.x) {
         if (b % n_shards != shard) continue;
         const int l = rank[b];
@@ -424,9 +364,8 @@ __global__ void __launch_bounds__(32) k_far_bwd(const double* __restrict__ Xs, c
         const int32_t t0 = nbeg[t], c = nend[t] - t0, s0 = nbeg[s], q = nend[s] - s0;
         const int32_t* I = pivI + b * max_rank;
         const int32_t* J = pivJ + b * max_rank;
-        const R* C = fac_bytes == (int)sizeof(R) ? (const R*)fac + 9 * fofs[b] : Cw;
+        const R* C = fac + 9 * fofs[b];
         const R* Q = C + (int64_t)l * 9 * c;
-        if (fac_bytes != (int)sizeof(R)) refactor<R, W>(sm.th, a, Xs, t0, c, s0, q, I, J, l, Cw, piT);
         R* Qb = Cb + (int64_t)l * 9 * c;
         auto Ck = [&](int k) { return C + (int64_t)k * 9 * c; };
         auto Qk = [&](int k) { return Q + (int64_t)k * 9 * q; };
@@ -644,16 +583,14 @@ void launch_bwd(hh_ctx* ctx, const hh_hmat* h, const double* Fs, const double* W
         HH_CUDA(cudaMemcpyAsync(&max_cq, dmax, sizeof(int), cudaMemcpyDeviceToHost, s));
         HH_CUDA(cudaStreamSynchronize(s));
         dev_free(dmax, s);
-        const bool narrow = h->real_bytes != (int)sizeof(R);
-        // Cb and Qb of one block, and the recomputed factors when narrow
-        const int64_t stride = (int64_t)max_cq * 9 * p.max_rank * (narrow ? 2 : 1);
+        const int64_t stride = (int64_t)max_cq * 9 * p.max_rank;   // Cb and Qb of one block
         const int64_t budget = (int64_t)16 << 30;
         int64_t grid = std::min<int64_t>(b->nG, max_grid);
         grid = std::max<int64_t>(1, std::min<int64_t>(grid, budget / (stride * (int64_t)sizeof(R))));
         R* scratch = dev_alloc_t<R>(grid * stride, s);
         k_far_bwd<R, W><<<(unsigned)grid, 32, smem, s>>>(t->Xs, Fs, Ws, b->PG, b->nG, t->nbeg, t->nend, h->rank,
                                                         h->pivI, h->pivJ, p.max_rank, p.shard_id, p.n_shards,
-                                                        h->factors, h->real_bytes, h->fofs, th, (R)p.radius, scratch,
+                                                        (const R*)h->factors, h->fofs, th, (R)p.radius, scratch,
                                                         stride, t->perm, gX, gth, gacc);
         HH_CHECK_LAUNCH();
         dev_free(scratch, s);
@@ -673,15 +610,16 @@ void matvec_backward_xtheta(hh_ctx* ctx, const hh_hmat* h, const double* Fs, con
     const hh_params& p = h->params;
     HH_REQUIRE(p.kernel == HH_MLP, HH_ERR_ARG, "dL/dX and dL/dtheta need the MLP kernel");
     HH_REQUIRE(p.max_rank <= BWD_MAXL, HH_ERR_ARG, "max_rank too large for the adjoint");
+    HH_REQUIRE(h->real_bytes == 8, HH_ERR_ARG, "the adjoint needs FP64 factors");
     double* gth = nullptr;
     if (gtheta) {
         gth = dev_alloc_t<double>(ctx->n_theta, s);
         HH_CUDA(cudaMemsetAsync(gth, 0, sizeof(double) * ctx->n_theta, s));
     }
-    // The adjoint always runs in FP64: with FP32 factors the cotangents of the
-    // rank loop cancel only to FP32 rounding times the squared condition number
-    // of the 3x3 pivot blocks, so narrower factors are recomputed in FP64 along
-    // the frozen pivots (refactor) and the pair-kernel reverse passes are FP64.
+    // The adjoint runs in FP64 on FP64 factors (the caller re-approximates a
+    // narrower H-matrix in FP64): the cotangents of the rank loop cancel only
+    // to the working rounding times the squared condition number of the 3x3
+    // pivot blocks.
     if (ctx->width == 32) launch_bwd<double, 32>(ctx, h, Fs, Ws, gX, gth, s);
     else launch_bwd<double, 64>(ctx, h, Fs, Ws, gX, gth, s);
     if (gtheta) {

@@ -124,16 +124,15 @@ def test_gtheta_central_differences(ctx):
 
 def test_gradient_close_to_dense_oracle(ctx):
     # the gradient of the approximant converges to the dense gradient with
-    # the ACA tolerance (about 10 zeta measured in FP64).  FP32 and BF16
-    # factors are recomputed in FP64 along their own pivots; those pivots are
-    # picked from FP32 residuals, which caps the gradient's accuracy near
-    # 2e-3 for this untrained MLP (and worsens as zeta nears the FP32 floor)
+    # the ACA tolerance (about 10 zeta measured in FP64).  For an FP32 or
+    # BF16 H-matrix, dL/dX and dL/dtheta are those of its FP64 counterpart
+    # (re-approximated inside the call); dL/dF is its own transpose product
     n = 2000
     X = hh_synth.rsa_cube(n, 0.1, seed=44)
     F, W = hh_synth.forces(n, 7), hh_synth.forces(n, 8)
     k = oracle.PairKernel("mlp", THETA, 32)
     gFo, gXo, gTo = oracle.dense_grad(X, F, W, k)
-    for prec, eps, tol in (("fp64", 1e-6, 1e-4), ("fp64", 1e-4, 3e-3), ("fp32", 1e-4, 5e-3), ("bf16", 1e-4, 5e-3)):
+    for prec, eps, tol in (("fp64", 1e-6, 1e-4), ("fp64", 1e-4, 3e-3), ("fp32", 1e-4, 3e-3), ("bf16", 1e-4, 3e-3)):
         gF, gX, gT, _ = grads(ctx, X, F, W, hh.Params(precision=prec, eps=eps))
         tf = 1e-3 if prec == "bf16" else tol    # BF16 near field: 1e-4-level entries
         assert np.linalg.norm(gF - gFo) <= tf * np.linalg.norm(gFo), prec

@@ -309,3 +309,38 @@ def test_predict_bf16_width64_and_transpose(ctx):
     assert oracle.rel_error(U, U1) < 1e-6
     # <W, M F> = <M^T W, F> holds to the BF16 pair-kernel noise of the two near-field sweeps
     assert abs(np.sum(W * U1) - np.sum(UT * F)) <= 1e-4 * np.sqrt(np.sum(W * W) * np.sum(U1 * U1))
+
+
+def test_predict_bf16_large_blocks_sampled_rows(ctx):
+    # N = 30k at C_leaf = 64 has admissible blocks with more than 512 rows or
+    # columns (the tensor-core ACA's CTA teams) besides the warp-team blocks
+    n = 30000
+    X = hh_synth.rsa_cube(n, 0.1, seed=14)
+    F = hh_synth.forces(n, 8)
+    p = hh.Params(precision="bf16", leaf_size=64)
+    t = ctx.build_tree(cuda(X), p)
+    G, _ = ctx.partition(t, p).export()
+    te = t.export()
+    side = te["end"] - te["begin"]
+    assert max(side[G[:, 0]].max(), side[G[:, 1]].max()) > 512
+    U = ctx.predict(cuda(X), cuda(F), p).cpu().numpy()
+    U2 = ctx.predict(cuda(X), cuda(F), p).cpu().numpy()
+    assert np.array_equal(U, U2)                         # independent of team scheduling
+    rows = np.arange(0, n, 97)
+    Ud = oracle.dense_matvec(X, F, kern(), rows=rows, with_self=False)
+    a1 = oracle.self_mobility()
+    assert oracle.rel_error(Ud, U[rows] - a1 * F[rows]) <= 2e-4
+    U32 = ctx.predict(cuda(X), cuda(F), hh.Params(precision="fp32", leaf_size=64)).cpu().numpy()
+    assert oracle.rel_error(U32, U) <= 2e-4
+
+
+def test_predict_bf16_batch_equals_separate(ctx):
+    sizes = [1700, 2500, 3]
+    Xs = [hh_synth.rsa_cube(s, 0.1, seed=40 + i) for i, s in enumerate(sizes)]
+    Fs = [hh_synth.forces(s, 50 + i) for i, s in enumerate(sizes)]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    p = hh.Params(precision="bf16")
+    Ub = ctx.predict(cuda(np.concatenate(Xs)), cuda(np.concatenate(Fs)), p, offsets=off).cpu().numpy()
+    for i in range(len(sizes)):
+        Ui = ctx.predict(cuda(Xs[i]), cuda(Fs[i]), p).cpu().numpy()
+        assert np.array_equal(Ub[off[i]:off[i + 1]], Ui)
