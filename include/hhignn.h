@@ -232,6 +232,44 @@ typedef struct {
 /* Counters of the last hh_predict / hh_aca on ctx. */
 hh_status hh_stats(hh_ctx *ctx, hh_stats_t *out);
 
+/* Launch shape of the block-ACA and near-field kernels (the paper fixes
+ * none; this is the B300 tuning surface).  0 in a field selects its default.
+ *   small_max      blocks with both sides <= small_max go to warp teams (32
+ *                  threads per block), the others to CTA teams; 32..512,
+ *                  default 512
+ *   aca_small_cps  CTAs per SM of the warp-team ACA kernel, 1..8, default 4
+ *   aca_large_cps  CTAs per SM of the CTA-team ACA kernel, 1..8, default 2
+ *                  (256-thread FP32 / FP64 kernel) or 4 (128-thread BF16
+ *                  tensor-core kernel)
+ *   near_cps       CTAs per SM of the tensor-core near-field kernel, 1..8,
+ *                  default 4
+ * Grids are further capped by the amount of work and the workspace budget;
+ * the SM's occupancy limits how many CTAs actually run at once. */
+typedef struct {
+    int32_t small_max;
+    int32_t aca_small_cps;
+    int32_t aca_large_cps;
+    int32_t near_cps;
+    int32_t reserved[4];   /* 0 */
+} hh_launch_cfg;
+
+/* Set / read ctx's launch shape (as stored: 0 = default).  Out-of-range
+ * fields: HH_ERR_ARG, nothing changed. */
+hh_status hh_set_launch(hh_ctx *ctx, const hh_launch_cfg *cfg);
+hh_status hh_get_launch(hh_ctx *ctx, hh_launch_cfg *cfg);
+
+/* Autotuner: times hh_predict on X_dev (FP64 [N,3] device, offsets / batch
+ * as in hh_predict, every force (1, 1, 1)) under p for candidate launch
+ * shapes and keeps the fastest on ctx (also written to *best when not NULL).
+ * Coordinate descent from ctx's current shape: each field in turn is swept
+ * over a fixed candidate list (small_max 128 / 256 / 512, aca_small_cps 1..4,
+ * aca_large_cps 1 / 2 / 4, near_cps 2 / 4 / 8) with the others held, and the
+ * value of the smallest median time over reps (>= 1) predictions is kept.
+ * Results do not depend on the launch shape beyond FP rounding order of the
+ * per-block partial sums (none: each block's output is written once). */
+hh_status hh_autotune(hh_ctx *ctx, const double *X_dev, const int64_t *offsets, int32_t batch, const hh_params *p,
+                      int32_t reps, void *stream, hh_launch_cfg *best);
+
 void hh_tree_free(hh_tree *t);
 void hh_blocks_free(hh_blocks *b);
 void hh_hmat_free(hh_hmat *h);

@@ -34,6 +34,7 @@ EXPORTS = [
     "hh_partition", "hh_aca", "hh_matvec", "hh_predict", "hh_matvec_backward", "hh_export_tree",
     "hh_export_blocks", "hh_export_aca", "hh_stats", "hh_tree_free", "hh_blocks_free", "hh_hmat_free",
     "hh_aca_block_apply_noalloc", "hh_eval_pairs", "hh_train_loss_grad", "hh_train_step",
+    "hh_set_launch", "hh_get_launch", "hh_autotune",
 ]
 
 
@@ -58,6 +59,14 @@ class CStats(ctypes.Structure):
                 ("n_blocks_G", ctypes.c_int64), ("n_blocks_H", ctypes.c_int64), ("n_nodes", ctypes.c_int64),
                 ("rank_hist", ctypes.c_int64 * 65), ("t_kernel_aca", ctypes.c_double),
                 ("t_kernel_near", ctypes.c_double), ("n_launches", ctypes.c_int64)]
+
+
+class CLaunch(ctypes.Structure):
+    _fields_ = [("small_max", ctypes.c_int32), ("aca_small_cps", ctypes.c_int32),
+                ("aca_large_cps", ctypes.c_int32), ("near_cps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 _P = ctypes.c_void_p
@@ -207,6 +216,25 @@ class Context:
                                         _dptr(U) if U is not None else None, r.shape[0], radius, lr,
                                         _stream(stream), ctypes.byref(loss)), "hh_train_step")
         return loss.value
+
+    # -- launch shape and autotuner ---------------------------------------------
+    def set_launch(self, small_max=0, aca_small_cps=0, aca_large_cps=0, near_cps=0):
+        c = CLaunch(small_max, aca_small_cps, aca_large_cps, near_cps)
+        self._check(lib().hh_set_launch(self._h, ctypes.byref(c)), "hh_set_launch")
+
+    def get_launch(self) -> dict:
+        c = CLaunch()
+        self._check(lib().hh_get_launch(self._h, ctypes.byref(c)), "hh_get_launch")
+        return c.as_dict()
+
+    def autotune(self, X, params: CParams, reps=1, offsets=None, stream=None) -> dict:
+        """Time hh_predict on X for candidate launch shapes; keep the fastest on this context."""
+        _check_xyz(X, "X")
+        off = np.asarray([0, X.shape[0]] if offsets is None else offsets, dtype=np.int64)
+        c = CLaunch()
+        self._check(lib().hh_autotune(self._h, _dptr(X), off.ctypes.data_as(_P), len(off) - 1, ctypes.byref(params),
+                                      int(reps), _stream(stream), ctypes.byref(c)), "hh_autotune")
+        return c.as_dict()
 
     def stats(self) -> dict:
         s = CStats()

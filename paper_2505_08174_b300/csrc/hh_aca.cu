@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(CTA_T) k_aca_cta(AcaArgs<R> A, int mode)
 
 // ---- work lists --------------------------------------------------------------
 __global__ void k_classify_blocks(const int32_t* __restrict__ PG, int64_t nG, const int32_t* __restrict__ nbeg,
-                                  const int32_t* __restrict__ nend, int shard, int n_shards,
+                                  const int32_t* __restrict__ nend, int shard, int n_shards, int small_max,
                                   int64_t* __restrict__ small_flag, int64_t* __restrict__ large_flag,
                                   uint64_t* __restrict__ large_key)
 {
@@ -313,7 +313,7 @@ __global__ void k_classify_blocks(const int32_t* __restrict__ PG, int64_t nG, co
     if (b >= nG) return;
     int32_t c = nend[PG[2 * b]] - nbeg[PG[2 * b]], q = nend[PG[2 * b + 1]] - nbeg[PG[2 * b + 1]];
     bool mine = (b % n_shards) == shard;
-    bool small = c <= SMALL_MAX && q <= SMALL_MAX;
+    bool small = c <= small_max && q <= small_max;
     small_flag[b] = mine && small;
     large_flag[b] = mine && !small;
     // larger blocks first: key = (2^31 - 1 - (c + q)) << 32 | b
@@ -352,7 +352,8 @@ __global__ void k_max_dim(const int32_t* __restrict__ work, int64_t n, const int
 
 template <typename R, int KIND>
 void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_small, const int32_t* work_large,
-                int64_t n_large, int max_small_cq, int max_large_cq, int mode, cudaStream_t s)
+                int64_t n_large, int max_small_cq, int max_large_cq, const hh_launch_cfg& lc, int mode,
+                cudaStream_t s)
 {
     const int th_bytes = A.n_th * (int)sizeof(R);
     const int mr = std::min(A.max_rank, MAXR);
@@ -362,7 +363,7 @@ void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_
         int64_t stride = (int64_t)max_large_cq * 9 * mr + ceil_div(max_large_cq, (int64_t)sizeof(R));
         stride = ceil_div(stride * (int64_t)sizeof(R), 256) * 256 / (int64_t)sizeof(R);
         const int64_t budget = (int64_t)24 << 30;  // bytes of large-team workspace
-        int64_t teams = std::min<int64_t>(n_large, 2 * ctx->n_sm);
+        int64_t teams = std::min<int64_t>(n_large, (int64_t)lc.aca_large_cps * ctx->n_sm);
         teams = std::max<int64_t>(1, std::min<int64_t>(teams, budget / (stride * (int64_t)sizeof(R))));
         R* scratch = dev_alloc_t<R>(stride * teams, s);
         HH_CUDA(cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), s));
@@ -381,7 +382,7 @@ void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_
         dev_free(scratch, s);
     }
     if (n_small > 0) {
-        int64_t blocks = std::min<int64_t>(ceil_div(n_small, WPB), 4 * ctx->n_sm);
+        int64_t blocks = std::min<int64_t>(ceil_div(n_small, WPB), (int64_t)lc.aca_small_cps * ctx->n_sm);
         int64_t teams = blocks * WPB;
         // factors (max_rank x 9 x (c+q) reals), rounded to 256 B
         int64_t stride = (int64_t)std::min(max_small_cq, 2 * SMALL_MAX) * 9 * mr;
@@ -487,8 +488,11 @@ void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_para
     int64_t* ol = dev_alloc_t<int64_t>(nG, s);
     uint64_t* key = dev_alloc_t<uint64_t>(nG, s);
     int64_t* tot = dev_alloc_t<int64_t>(2, s);
+    const bool use_tc = p.precision == HH_BF16 && kernel_kind(p, ctx->width) < 2;
+    const hh_launch_cfg lc = resolved_launch(ctx, use_tc);
     k_classify_blocks<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(bl->PG, nG, t->nbeg, t->nend, p.shard_id,
-                                                                  p.n_shards, fs, fl, key);
+                                                                  p.n_shards, std::min(lc.small_max, SMALL_MAX), fs,
+                                                                  fl, key);
     HH_CHECK_LAUNCH();
     dev_scan_i64(fs, os, nG, tot, s);
     dev_scan_i64(fl, ol, nG, tot + 1, s);
@@ -529,16 +533,16 @@ void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_para
     const int max_small_cq = dims[0];
     const int kind = kernel_kind(p, ctx->width);
     if constexpr (sizeof(R) == 4) {
-        if (p.precision == HH_BF16 && kind < 2) {
+        if (use_tc) {
             aca_tc_run(ctx, t, bl, p, r, ws, h[0], wl, h[1], max_small_cq, max_cq, s);
             dev_free(fs, s); dev_free(fl, s); dev_free(os, s); dev_free(ol, s); dev_free(key, s); dev_free(tot, s);
             dev_free(ws, s); dev_free(wl, s);
             return;
         }
     }
-    if (kind == 0) launch_aca<R, 0>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, r.mode, s);
-    else if (kind == 1) launch_aca<R, 1>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, r.mode, s);
-    else launch_aca<R, 2>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, r.mode, s);
+    if (kind == 0) launch_aca<R, 0>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, lc, r.mode, s);
+    else if (kind == 1) launch_aca<R, 1>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, lc, r.mode, s);
+    else launch_aca<R, 2>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, lc, r.mode, s);
     dev_free(fs, s); dev_free(fl, s); dev_free(os, s); dev_free(ol, s); dev_free(key, s); dev_free(tot, s);
     dev_free(ws, s); dev_free(wl, s);
 }

@@ -4,22 +4,19 @@
 // the norm recurrence in FP64).
 //
 // The rank loop is the one of hh_aca.cu (same pivot rules, stopping test and
-// outputs); what changes is who evaluates the pair kernel.  A CTA of 128
-// threads owns one 128-row MLP tile (hh_tcmlp.cuh) and runs in lockstep
-// "rounds": in every round each thread contributes one query (a separation
-// x_m - x_n of the column or row being generated), the tile goes through the
-// four MLP layers on tcgen05, and each thread gets back the 3x3 entry of its
-// own query.  Between rounds the teams run their own rank loops:
-//   * warp teams (blocks with c, q <= 512): 4 teams per CTA, each fills its
-//     32 tile rows (TMEM lanes 32w..32w+31, the warp's own quadrant) with 32
-//     consecutive rows or columns of its current block and runs the MLP
-//     chain on its own (hh_tcmlp.cuh: per-warp MMAs into per-warp TMEM
-//     columns), so the warps never wait for one another;
-//   * one CTA team (larger blocks): the whole tile serves one block, in
-//     lockstep rounds of 128 queries.
-// A team whose pass is complete does its pivot / Gram / stopping work
-// between two of its rounds; a CTA team without work submits dummy rows
-// until every team has found the work list empty.
+// outputs); what changes is who evaluates the pair kernel.  A CTA has 128
+// threads and one shared 128-row MLP tile (hh_tcmlp.cuh); every warp owns
+// the tile rows of its TMEM quadrant (32w..32w+31) and runs the four MLP
+// layers for them on its own: it writes one query per lane (a separation
+// x_m - x_n of the column or row being generated), issues the MMAs into its
+// own TMEM columns, waits on its own mbarrier and reads back its lanes.  No
+// warp waits for another while queries are evaluated.  Teams:
+//   * warp teams (blocks with c, q <= small_max): 4 teams per CTA, each takes
+//     32 consecutive rows or columns of its current block per round;
+//   * one CTA team (larger blocks): the 4 warps share one block, 128 rows or
+//     columns per round, and meet only at the end of each pass.
+// A team whose pass is complete does its pivot / Gram / stopping work before
+// its next round.
 #include <algorithm>
 
 #include "hh_aca.cuh"
@@ -37,45 +34,37 @@ struct alignas(128) AcaTcSmem {
     int failw[4];
 };
 
-// TMEM columns of a CTA: one W-column accumulator (CTA team) or one per warp.
-template <int W, bool CTA>
-__host__ __device__ constexpr uint32_t aca_tmem_cols() { return CTA ? (W <= 32 ? 32u : 64u) : (W <= 32 ? 128u : 256u); }
+// TMEM columns of a CTA: one W-column accumulator per warp.
+template <int W>
+__host__ __device__ constexpr uint32_t aca_tmem_cols() { return W <= 32 ? 128u : 256u; }
 
-template <int W, bool CTA, class S>
+template <int W, class S>
 __device__ void aca_tc_setup(S& sm, const float* th)
 {
-    if constexpr (CTA) {
-        tc_setup<W>(sm.tc, th);
-    } else {
-        tc_load_weights<W>(sm.tc, th);
-        if (threadIdx.x == 0)
-            for (int w = 0; w < 4; ++w) { mbar_init(&sm.mbw[w], 1); sm.failw[w] = 0; }
-        if (threadIdx.x < 32) {
-            tmem_alloc(&sm.tc.tmem, aca_tmem_cols<W, CTA>());
-            tmem_relinquish();
-        }
-        tc_fence_before();
-        __syncthreads();
-        tc_fence_after();
+    tc_load_weights<W>(sm.tc, th);
+    if (threadIdx.x == 0)
+        for (int w = 0; w < 4; ++w) { mbar_init(&sm.mbw[w], 1); sm.failw[w] = 0; }
+    if (threadIdx.x < 32) {
+        tmem_alloc(&sm.tc.tmem, aca_tmem_cols<W>());
+        tmem_relinquish();
     }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 }
 
-template <int W, bool CTA, class S>
+template <int W, class S>
 __device__ void aca_tc_teardown(S& sm)
 {
-    if constexpr (CTA) {
-        tc_teardown<W>(sm.tc);
-    } else {
-        tc_fence_before();
-        __syncthreads();
-        // a warp that timed out gives its MMA group one more bounded wait
-        // before the accumulator columns are released
-        const int w = threadIdx.x >> 5;
-        if ((threadIdx.x & 31) == 0 && sm.failw[w]) mbar_wait_bounded(&sm.mbw[w], sm.pend[w], TC_WAIT_LIMIT);
-        __syncthreads();
-        tc_fence_after();
-        if (threadIdx.x < 32) tmem_dealloc(sm.tc.tmem, aca_tmem_cols<W, CTA>());
-    }
+    tc_fence_before();
+    __syncthreads();
+    // a warp that timed out gives its MMA group one more bounded wait before
+    // the accumulator columns are released
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0 && sm.failw[w]) mbar_wait_bounded(&sm.mbw[w], sm.pend[w], TC_WAIT_LIMIT);
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x < 32) tmem_dealloc(sm.tc.tmem, aca_tmem_cols<W>());
 }
 
 template <int W, class Team>
@@ -84,23 +73,24 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
     constexpr int NT = TC_T / Team::SIZE;
     constexpr int SIZE = Team::SIZE, ROWS = Team::ROWS;
     constexpr bool REG = Team::REG_FLAGS;
-    constexpr bool CTA = NT == 1;   // CTA team: lockstep tiles; warp teams: independent warps
+    constexpr bool CTA = NT == 1;   // one 128-thread team per CTA, else 4 warp teams
     extern __shared__ __align__(128) unsigned char smem_raw[];
     AcaTcSmem<W, Team>& S = *reinterpret_cast<AcaTcSmem<W, Team>*>(smem_raw);
-    aca_tc_setup<W, CTA>(S, th_packed);
+    aca_tc_setup<W>(S, th_packed);
     const Team tm;
     const int team = threadIdx.x / SIZE;
     const int tid = tm.tid();
     TeamSmem<float>& sm = S.team[team];
     float* const ws = A.scratch + ((int64_t)blockIdx.x * NT + team) * A.team_stride;
     const float a = (float)A.pp.a;
-    uint32_t phase = 0;
-    TcWarp tw{S.tc.tmem + (uint32_t)(W * team), &S.mbw[team & 3], 0u, &S.failw[team & 3], &S.pend[team & 3]};
+    const int warp = threadIdx.x >> 5;   // TMEM quadrant, accumulator columns and mbarrier of this warp
+    TcWarp tw{S.tc.tmem + (uint32_t)(W * warp), &S.mbw[warp], 0u, &S.failw[warp], &S.pend[warp]};
 
     // state of the team's current block (uniform over the team; lam2 is
     // maintained by thread 0 only)
     int64_t b = -1;
     bool exhausted = false;
+    bool failed = false;
     int32_t t0 = 0, c = 0, s0 = 0, q = 0;
     int kmax = 0, k = 0, pass = 0, x0 = 0, j = 0, bi = -1;
     double lam2 = 0.0;
@@ -222,14 +212,15 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
             f[0] = 1.f; f[1] = f[2] = 0.f; f[3] = a;
         }
         float o[6];
-        if constexpr (CTA) {
+        if (exhausted) break;   // uniform over the team
+        // warps without a valid row skip the chain; a warp whose chain timed
+        // out stops issuing MMAs (a CTA team leaves at the end of the pass)
+        if (!failed && __any_sync(0xffffffffu, valid)) {
             tc_write_features<W>(S.tc, threadIdx.x, f);
-            if (__syncthreads_and(exhausted)) break;
-            if (!tc_mlp_tile<W>(S.tc, phase, A.status, o)) break;
-        } else {
-            if (exhausted) break;
-            tc_write_features<W>(S.tc, threadIdx.x, f);
-            if (!tcw_mlp_rows<W>(S.tc, tw, A.status, o)) break;
+            if (!tcw_mlp_rows<W>(S.tc, tw, A.status, o)) failed = true;
+        }
+        if constexpr (!CTA) {
+            if (failed) break;
         }
         // ---- residual entry, stored in the factor being extended
         if (valid) {
@@ -259,7 +250,11 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
         if (b < 0 || x0 < nx) continue;
 
         // ---- end of a pass (team-uniform)
-        tm.sync();
+        if constexpr (CTA) {
+            if (__syncthreads_or(failed)) break;
+        } else {
+            tm.sync();
+        }
         if (pass == 0) {
             tm.argmax(best, barg, sm);
             if (barg < 0 || !(best > 0.f)) { finish(k, false); continue; }
@@ -348,7 +343,7 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
             tm.sync();
         }
     }
-    aca_tc_teardown<W, CTA>(S);
+    aca_tc_teardown<W>(S);
 }
 
 template <int W, class Team>
@@ -371,12 +366,13 @@ void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_par
 {
     HH_REQUIRE(p.kernel == HH_MLP && p.precision == HH_BF16, HH_ERR_ARG, "tensor-core ACA needs the BF16 MLP kernel");
     const int mr = std::min(p.max_rank, MAXR);
+    const hh_launch_cfg lc = resolved_launch(ctx, true);
     AcaArgs<float> A = make_aca_args<float>(ctx, t, bl, p, r);
     if (n_large > 0) {
         int64_t stride = (int64_t)max_large_cq * 9 * mr + ceil_div(max_large_cq, (int64_t)sizeof(float));
         stride = ceil_div(stride * (int64_t)sizeof(float), 256) * 256 / (int64_t)sizeof(float);
         const int64_t budget = (int64_t)24 << 30;
-        int64_t teams = std::min<int64_t>(n_large, 4 * ctx->n_sm);
+        int64_t teams = std::min<int64_t>(n_large, (int64_t)lc.aca_large_cps * ctx->n_sm);
         teams = std::max<int64_t>(1, std::min<int64_t>(teams, budget / (stride * (int64_t)sizeof(float))));
         float* scratch = dev_alloc_t<float>(stride * teams, s);
         HH_CUDA(cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), s));
@@ -394,7 +390,7 @@ void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_par
     }
     if (n_small > 0) {
         constexpr int NT = TC_T / 32;
-        const int64_t blocks = std::min<int64_t>(ceil_div(n_small, NT), 4 * ctx->n_sm);
+        const int64_t blocks = std::min<int64_t>(ceil_div(n_small, NT), (int64_t)lc.aca_small_cps * ctx->n_sm);
         int64_t stride = (int64_t)std::min(max_small_cq, 2 * SMALL_MAX) * 9 * mr;
         stride = ceil_div(stride * (int64_t)sizeof(float), 256) * 256 / (int64_t)sizeof(float);
         float* scratch = dev_alloc_t<float>(stride * blocks * NT, s);

@@ -11,6 +11,9 @@
 #include <algorithm>
 #include <new>
 
+#include <algorithm>
+#include <vector>
+
 #include "hh_internal.h"
 
 namespace {
@@ -59,6 +62,12 @@ void check_params(const hh_ctx* ctx, const hh_params* p)
     HH_REQUIRE(p->radius > 0.0 && p->viscosity > 0.0, HH_ERR_ARG, "radius and viscosity must be > 0");
     HH_REQUIRE(p->n_shards >= 1 && p->shard_id >= 0 && p->shard_id < p->n_shards, HH_ERR_ARG, "bad shard");
     HH_REQUIRE(p->j1_rule == 0 || p->j1_rule == 1, HH_ERR_ARG, "j1_rule must be 0 or 1");
+}
+
+__global__ void k_fill(double* __restrict__ a, int64_t n, double v)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = v;
 }
 
 template <typename F>
@@ -611,6 +620,97 @@ hh_status hh_stats(hh_ctx* ctx, hh_stats_t* out)
         *out = ctx->stats;
         return HH_OK;
     });
+}
+
+hh_status hh_set_launch(hh_ctx* ctx, const hh_launch_cfg* cfg)
+{
+    if (!ctx || !cfg) return HH_ERR_ARG;
+    return guarded(ctx, [&]() {
+        HH_REQUIRE(cfg->small_max == 0 || (cfg->small_max >= 32 && cfg->small_max <= 512), HH_ERR_ARG,
+                   "small_max must be 0 or in [32, 512]");
+        auto ok = [](int32_t v) { return v >= 0 && v <= 8; };
+        HH_REQUIRE(ok(cfg->aca_small_cps) && ok(cfg->aca_large_cps) && ok(cfg->near_cps), HH_ERR_ARG,
+                   "CTAs per SM must be 0 or in [1, 8]");
+        for (int i = 0; i < 4; ++i) HH_REQUIRE(cfg->reserved[i] == 0, HH_ERR_ARG, "reserved fields must be 0");
+        ctx->launch = *cfg;
+        return HH_OK;
+    });
+}
+
+hh_status hh_get_launch(hh_ctx* ctx, hh_launch_cfg* cfg)
+{
+    if (!ctx || !cfg) return HH_ERR_ARG;
+    *cfg = ctx->launch;
+    return HH_OK;
+}
+
+hh_status hh_autotune(hh_ctx* ctx, const double* X_dev, const int64_t* offsets, int32_t batch, const hh_params* p,
+                      int32_t reps, void* stream, hh_launch_cfg* best)
+{
+    if (!ctx || !X_dev || !offsets || !p || batch < 1) return HH_ERR_ARG;
+    const int64_t n = offsets[batch];
+    if (n < 1) return HH_ERR_ARG;
+    if (reps < 1) reps = 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* F = nullptr;
+    double* U = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    hh_status st = guarded(ctx, [&]() {
+        HH_CUDA(cudaMalloc(&F, sizeof(double) * 3 * n));
+        HH_CUDA(cudaMalloc(&U, sizeof(double) * 3 * n));
+        k_fill<<<(unsigned)ceil_div(3 * n, 256), 256, 0, s>>>(F, 3 * n, 1.0);
+        HH_CHECK_LAUNCH();
+        HH_CUDA(cudaEventCreate(&e0));
+        HH_CUDA(cudaEventCreate(&e1));
+        return HH_OK;
+    });
+    // median time of reps predictions (after one untimed run) under cfg
+    auto score = [&](const hh_launch_cfg& cfg, double* ms) -> hh_status {
+        ctx->launch = cfg;
+        std::vector<double> t;
+        for (int r = 0; r <= reps; ++r) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) return HH_ERR_CUDA;
+            hh_status q = hh_predict(ctx, X_dev, F, offsets, batch, p, stream, U);
+            if (q != HH_OK) return q;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return HH_ERR_CUDA;
+            float v = 0.f;
+            if (cudaEventElapsedTime(&v, e0, e1) != cudaSuccess) return HH_ERR_CUDA;
+            if (r > 0) t.push_back(v);
+        }
+        std::sort(t.begin(), t.end());
+        *ms = t[t.size() / 2];
+        return HH_OK;
+    };
+    const hh_launch_cfg start = ctx->launch;
+    hh_launch_cfg cur = start;
+    double cur_ms = 0.0;
+    if (st == HH_OK) st = score(cur, &cur_ms);
+    static const int32_t cand_small_max[] = {128, 256, 512};
+    static const int32_t cand_small_cps[] = {1, 2, 3, 4};
+    static const int32_t cand_large_cps[] = {1, 2, 4};
+    static const int32_t cand_near_cps[] = {2, 4, 8};
+    struct Field { int32_t hh_launch_cfg::*f; const int32_t* v; int nv; };
+    const Field fields[] = {{&hh_launch_cfg::small_max, cand_small_max, 3},
+                            {&hh_launch_cfg::aca_small_cps, cand_small_cps, 4},
+                            {&hh_launch_cfg::aca_large_cps, cand_large_cps, 3},
+                            {&hh_launch_cfg::near_cps, cand_near_cps, 3}};
+    for (const Field& fd : fields) {
+        for (int i = 0; i < fd.nv && st == HH_OK; ++i) {
+            hh_launch_cfg c = cur;
+            if (c.*fd.f == fd.v[i]) continue;
+            c.*fd.f = fd.v[i];
+            double ms = 0.0;
+            st = score(c, &ms);
+            if (st == HH_OK && ms < cur_ms) { cur = c; cur_ms = ms; }
+        }
+    }
+    ctx->launch = st == HH_OK ? cur : start;
+    if (st == HH_OK && best) *best = cur;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (F) cudaFree(F);
+    if (U) cudaFree(U);
+    return st;
 }
 
 void hh_tree_free(hh_tree* t) { free_tree(t); }

@@ -28,7 +28,19 @@ struct hh_ctx {
     int kev_aca_used = 0;                // ACA kernel event pairs recorded this call
     int kev_near_used = 0;
     unsigned long long launch_base = 0;  // g_hh_launches at the start of the call
+    hh_launch_cfg launch{};              // 0 fields: defaults (see resolved_launch)
 };
+
+// Launch shape with defaults filled in; tc selects the tensor-core defaults.
+inline hh_launch_cfg resolved_launch(const hh_ctx* ctx, bool tc)
+{
+    hh_launch_cfg c = ctx->launch;
+    if (c.small_max <= 0) c.small_max = 512;
+    if (c.aca_small_cps <= 0) c.aca_small_cps = 4;
+    if (c.aca_large_cps <= 0) c.aca_large_cps = tc ? 4 : 2;
+    if (c.near_cps <= 0) c.near_cps = 4;
+    return c;
+}
 
 struct hh_tree {
     hh_ctx* ctx = nullptr;

@@ -160,7 +160,7 @@ void near_field_tc(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_p
 {
     HH_REQUIRE(p.kernel == HH_MLP, HH_ERR_ARG, "the tensor-core path evaluates the MLP kernel only");
     HH_REQUIRE(p.leaf_size <= 129, HH_ERR_ARG, "leaf_size must be <= 129");
-    const int64_t grid = std::min<int64_t>(n_work, (int64_t)ctx->n_sm * 4);
+    const int64_t grid = std::min<int64_t>(n_work, (int64_t)ctx->n_sm * resolved_launch(ctx, true).near_cps);
     HH_CUDA(cudaEventRecord(ctx->kev[4], s));
     if (ctx->width == 32) {
         const size_t smem = near_smem_bytes<32>();
