@@ -25,6 +25,7 @@
 // The 3x3 Gram sums are formed and reduced in the working precision; nu^2,
 // the cross term and the lambda^2 recurrence are reduced and kept in FP64.
 #include <algorithm>
+#include <vector>
 
 #include "hh_aca.cuh"
 
@@ -350,36 +351,60 @@ __global__ void k_max_dim(const int32_t* __restrict__ work, int64_t n, const int
     atomicMax(out, c + q);
 }
 
+// Size classes of the sorted large list (keys: (2^31 - 1 - (c + q)) << 32 | b,
+// ascending = decreasing c + q): pos[i] = first item with c + q <= lim[i],
+// mx[i] = c + q of item pos[i - 1] (class i's largest), mx[0] = the first item's.
+constexpr int N_CLASS_LIMITS = 3;
+__constant__ int32_t c_class_lim[N_CLASS_LIMITS] = {16384, 4096, 1536};
+
+__global__ void k_class_bounds(const uint64_t* __restrict__ key, int64_t n, int64_t* __restrict__ pos,
+                               int32_t* __restrict__ mx)
+{
+    const int i = threadIdx.x;
+    auto cq = [&](int64_t x) { return (int32_t)(0x7fffffffu - (uint32_t)(key[x] >> 32)); };
+    if (i < N_CLASS_LIMITS) {
+        int64_t lo = 0, hi = n;   // first x with cq(x) <= lim
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (cq(mid) <= c_class_lim[i]) hi = mid; else lo = mid + 1;
+        }
+        pos[i] = lo;
+        mx[i + 1] = lo < n ? cq(lo) : 0;
+    }
+    if (i == 0) mx[0] = n > 0 ? cq(0) : 0;
+}
+
 template <typename R, int KIND>
 void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_small, const int32_t* work_large,
-                int64_t n_large, int max_small_cq, int max_large_cq, const hh_launch_cfg& lc, int mode,
-                cudaStream_t s)
+                const std::vector<AcaClass>& cls, int max_small_cq, const hh_launch_cfg& lc, int mode, cudaStream_t s)
 {
     const int th_bytes = A.n_th * (int)sizeof(R);
     const int mr = std::min(A.max_rank, MAXR);
     // large blocks first (CTA teams), then small blocks (warp teams)
-    if (n_large > 0) {
-        // factors (max_rank x 9 x (c+q) reals) + c+q flag bytes, rounded to 256 B
-        int64_t stride = (int64_t)max_large_cq * 9 * mr + ceil_div(max_large_cq, (int64_t)sizeof(R));
-        stride = ceil_div(stride * (int64_t)sizeof(R), 256) * 256 / (int64_t)sizeof(R);
-        const int64_t budget = (int64_t)24 << 30;  // bytes of large-team workspace
-        int64_t teams = std::min<int64_t>(n_large, (int64_t)lc.aca_large_cps * ctx->n_sm);
-        teams = std::max<int64_t>(1, std::min<int64_t>(teams, budget / (stride * (int64_t)sizeof(R))));
-        R* scratch = dev_alloc_t<R>(stride * teams, s);
-        HH_CUDA(cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), s));
-        AcaArgs<R> B = A;
-        B.work = work_large;
-        B.n_work = n_large;
-        B.scratch = scratch;
-        B.team_stride = stride;
+    if (!cls.empty()) {
         size_t smem = sizeof(TeamSmem<R>) + th_bytes + sizeof(R) * act_floats_per_warp<R, KIND>() * (CTA_T / 32);
         HH_CUDA(cudaFuncSetAttribute(k_aca_cta<R, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         HH_CUDA(cudaEventRecord(ctx->kev[0], s));
-        k_aca_cta<R, KIND><<<(unsigned)teams, CTA_T, smem, s>>>(B, mode);
-        HH_CHECK_LAUNCH();
+        for (const AcaClass& k : cls) {
+            // factors (max_rank x 9 x (c+q) reals) + c+q flag bytes, rounded to 256 B
+            int64_t stride = (int64_t)k.max_cq * 9 * mr + ceil_div(k.max_cq, (int64_t)sizeof(R));
+            stride = ceil_div(stride * (int64_t)sizeof(R), 256) * 256 / (int64_t)sizeof(R);
+            const int64_t budget = (int64_t)24 << 30;  // bytes of large-team workspace
+            int64_t teams = std::min<int64_t>(k.end - k.begin, (int64_t)lc.aca_large_cps * ctx->n_sm);
+            teams = std::max<int64_t>(1, std::min<int64_t>(teams, budget / (stride * (int64_t)sizeof(R))));
+            R* scratch = dev_alloc_t<R>(stride * teams, s);
+            HH_CUDA(cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), s));
+            AcaArgs<R> B = A;
+            B.work = work_large + k.begin;
+            B.n_work = k.end - k.begin;
+            B.scratch = scratch;
+            B.team_stride = stride;
+            k_aca_cta<R, KIND><<<(unsigned)teams, CTA_T, smem, s>>>(B, mode);
+            HH_CHECK_LAUNCH();
+            dev_free(scratch, s);
+        }
         HH_CUDA(cudaEventRecord(ctx->kev[1], s));
         ctx->kev_aca_used |= 1;
-        dev_free(scratch, s);
     }
     if (n_small > 0) {
         int64_t blocks = std::min<int64_t>(ceil_div(n_small, WPB), (int64_t)lc.aca_small_cps * ctx->n_sm);
@@ -503,6 +528,7 @@ void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_para
     int32_t* wl = dev_alloc_t<int32_t>(h[1], s);
     k_compact<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(fs, os, nG, ws);
     HH_CHECK_LAUNCH();
+    std::vector<AcaClass> cls;   // size classes of the large list
     if (h[1] > 0) {
         uint64_t* lk = dev_alloc_t<uint64_t>(h[1], s);
         k_compact_keys<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(fl, ol, key, nG, lk);
@@ -510,39 +536,49 @@ void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_para
         dev_radix_sort(lk, nullptr, h[1], 64, s);
         k_keys_to_work<<<(unsigned)ceil_div(h[1], 256), 256, 0, s>>>(lk, h[1], wl);
         HH_CHECK_LAUNCH();
+        int64_t* cpos = dev_alloc_t<int64_t>(N_CLASS_LIMITS, s);
+        int32_t* cmx = dev_alloc_t<int32_t>(N_CLASS_LIMITS + 1, s);
+        k_class_bounds<<<1, 32, 0, s>>>(lk, h[1], cpos, cmx);
+        HH_CHECK_LAUNCH();
+        int64_t hp[N_CLASS_LIMITS];
+        int32_t hm[N_CLASS_LIMITS + 1];
+        HH_CUDA(cudaMemcpyAsync(hp, cpos, sizeof hp, cudaMemcpyDeviceToHost, s));
+        HH_CUDA(cudaMemcpyAsync(hm, cmx, sizeof hm, cudaMemcpyDeviceToHost, s));
+        HH_CUDA(cudaStreamSynchronize(s));
+        int64_t b0 = 0;
+        for (int i = 0; i <= N_CLASS_LIMITS; ++i) {
+            const int64_t e = i < N_CLASS_LIMITS ? hp[i] : h[1];
+            if (e > b0) cls.push_back(AcaClass{b0, e, hm[i == 0 ? 0 : i]});
+            b0 = std::max(b0, e);
+        }
+        dev_free(cpos, s);
+        dev_free(cmx, s);
         dev_free(lk, s);
     }
-    // largest c + q of each list: sizes the per-team factor workspaces
-    int dims[2] = {0, 0};
-    if (h[0] + h[1] > 0) {
-        int* dmax = dev_alloc_t<int>(2, s);
-        HH_CUDA(cudaMemsetAsync(dmax, 0, 2 * sizeof(int), s));
-        if (h[0] > 0) {
-            k_max_dim<<<(unsigned)ceil_div(h[0], 256), 256, 0, s>>>(ws, h[0], bl->PG, t->nbeg, t->nend, dmax);
-            HH_CHECK_LAUNCH();
-        }
-        if (h[1] > 0) {
-            k_max_dim<<<(unsigned)ceil_div(h[1], 256), 256, 0, s>>>(wl, h[1], bl->PG, t->nbeg, t->nend, dmax + 1);
-            HH_CHECK_LAUNCH();
-        }
+    // largest c + q of the small list: sizes the warp teams' factor workspaces
+    int dims[1] = {0};
+    if (h[0] > 0) {
+        int* dmax = dev_alloc_t<int>(1, s);
+        HH_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int), s));
+        k_max_dim<<<(unsigned)ceil_div(h[0], 256), 256, 0, s>>>(ws, h[0], bl->PG, t->nbeg, t->nend, dmax);
+        HH_CHECK_LAUNCH();
         HH_CUDA(cudaMemcpyAsync(dims, dmax, sizeof dims, cudaMemcpyDeviceToHost, s));
         HH_CUDA(cudaStreamSynchronize(s));
         dev_free(dmax, s);
     }
-    const int max_cq = dims[1];
     const int max_small_cq = dims[0];
     const int kind = kernel_kind(p, ctx->width);
     if constexpr (sizeof(R) == 4) {
         if (use_tc) {
-            aca_tc_run(ctx, t, bl, p, r, ws, h[0], wl, h[1], max_small_cq, max_cq, s);
+            aca_tc_run(ctx, t, bl, p, r, ws, h[0], wl, cls.data(), (int)cls.size(), max_small_cq, s);
             dev_free(fs, s); dev_free(fl, s); dev_free(os, s); dev_free(ol, s); dev_free(key, s); dev_free(tot, s);
             dev_free(ws, s); dev_free(wl, s);
             return;
         }
     }
-    if (kind == 0) launch_aca<R, 0>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, lc, r.mode, s);
-    else if (kind == 1) launch_aca<R, 1>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, lc, r.mode, s);
-    else launch_aca<R, 2>(ctx, A, ws, h[0], wl, h[1], max_small_cq, max_cq, lc, r.mode, s);
+    if (kind == 0) launch_aca<R, 0>(ctx, A, ws, h[0], wl, cls, max_small_cq, lc, r.mode, s);
+    else if (kind == 1) launch_aca<R, 1>(ctx, A, ws, h[0], wl, cls, max_small_cq, lc, r.mode, s);
+    else launch_aca<R, 2>(ctx, A, ws, h[0], wl, cls, max_small_cq, lc, r.mode, s);
     dev_free(fs, s); dev_free(fl, s); dev_free(os, s); dev_free(ol, s); dev_free(key, s); dev_free(tot, s);
     dev_free(ws, s); dev_free(wl, s);
 }

@@ -361,32 +361,35 @@ void launch_tc(hh_ctx* ctx, const AcaArgs<float>& A, int64_t grid, int mode, cud
 // launches in hh_aca.cu): large blocks (c or q > 512, by decreasing size)
 // on CTA teams, then small blocks on warp teams.
 void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_params& p, const AcaRun& r,
-                const int32_t* work_small, int64_t n_small, const int32_t* work_large, int64_t n_large,
-                int max_small_cq, int max_large_cq, cudaStream_t s)
+                const int32_t* work_small, int64_t n_small, const int32_t* work_large, const AcaClass* cls,
+                int n_cls, int max_small_cq, cudaStream_t s)
 {
     HH_REQUIRE(p.kernel == HH_MLP && p.precision == HH_BF16, HH_ERR_ARG, "tensor-core ACA needs the BF16 MLP kernel");
     const int mr = std::min(p.max_rank, MAXR);
     const hh_launch_cfg lc = resolved_launch(ctx, true);
     AcaArgs<float> A = make_aca_args<float>(ctx, t, bl, p, r);
-    if (n_large > 0) {
-        int64_t stride = (int64_t)max_large_cq * 9 * mr + ceil_div(max_large_cq, (int64_t)sizeof(float));
-        stride = ceil_div(stride * (int64_t)sizeof(float), 256) * 256 / (int64_t)sizeof(float);
-        const int64_t budget = (int64_t)24 << 30;
-        int64_t teams = std::min<int64_t>(n_large, (int64_t)lc.aca_large_cps * ctx->n_sm);
-        teams = std::max<int64_t>(1, std::min<int64_t>(teams, budget / (stride * (int64_t)sizeof(float))));
-        float* scratch = dev_alloc_t<float>(stride * teams, s);
-        HH_CUDA(cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), s));
-        AcaArgs<float> B = A;
-        B.work = work_large;
-        B.n_work = n_large;
-        B.scratch = scratch;
-        B.team_stride = stride;
+    if (n_cls > 0) {
         HH_CUDA(cudaEventRecord(ctx->kev[0], s));
-        if (ctx->width == 32) launch_tc<32, CtaTeamT<TC_T>>(ctx, B, teams, r.mode, s);
-        else launch_tc<64, CtaTeamT<TC_T>>(ctx, B, teams, r.mode, s);
+        for (int i = 0; i < n_cls; ++i) {
+            const AcaClass& k = cls[i];
+            int64_t stride = (int64_t)k.max_cq * 9 * mr + ceil_div(k.max_cq, (int64_t)sizeof(float));
+            stride = ceil_div(stride * (int64_t)sizeof(float), 256) * 256 / (int64_t)sizeof(float);
+            const int64_t budget = (int64_t)24 << 30;
+            int64_t teams = std::min<int64_t>(k.end - k.begin, (int64_t)lc.aca_large_cps * ctx->n_sm);
+            teams = std::max<int64_t>(1, std::min<int64_t>(teams, budget / (stride * (int64_t)sizeof(float))));
+            float* scratch = dev_alloc_t<float>(stride * teams, s);
+            HH_CUDA(cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), s));
+            AcaArgs<float> B = A;
+            B.work = work_large + k.begin;
+            B.n_work = k.end - k.begin;
+            B.scratch = scratch;
+            B.team_stride = stride;
+            if (ctx->width == 32) launch_tc<32, CtaTeamT<TC_T>>(ctx, B, teams, r.mode, s);
+            else launch_tc<64, CtaTeamT<TC_T>>(ctx, B, teams, r.mode, s);
+            dev_free(scratch, s);
+        }
         HH_CUDA(cudaEventRecord(ctx->kev[1], s));
         ctx->kev_aca_used |= 1;
-        dev_free(scratch, s);
     }
     if (n_small > 0) {
         constexpr int NT = TC_T / 32;

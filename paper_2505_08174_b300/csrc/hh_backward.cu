@@ -36,7 +36,6 @@ struct Rec {  // per-entry record of one lane
 };
 
 template <typename R> __device__ __forceinline__ R sig_(R x);
-template <> __device__ __forceinline__ float sig_<float>(float x) { return 1.0f / (1.0f + __expf(-x)); }
 template <> __device__ __forceinline__ double sig_<double>(double x) { return 1.0 / (1.0 + exp(-x)); }
 
 template <int W>

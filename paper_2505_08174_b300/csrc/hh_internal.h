@@ -136,11 +136,20 @@ struct AcaRun {
 void aca_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_params& p, const AcaRun& r,
              cudaStream_t s);
 
+// A size class of the large-block work list (sorted by decreasing c + q):
+// items begin .. end - 1, the largest with c + q = max_cq.  Each class gets
+// its own workspace stride, so the many mid-size blocks are not held to the
+// team count the few largest blocks allow.
+struct AcaClass {
+    int64_t begin, end;
+    int32_t max_cq;
+};
+
 // Tensor-core ACA (hh_aca_tc.cu, precision HH_BF16 with the MLP kernel) over
 // the small (warp-team) and large (CTA-team) work lists built by aca_run.
 void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_params& p, const AcaRun& r,
-                const int32_t* work_small, int64_t n_small, const int32_t* work_large, int64_t n_large,
-                int max_small_cq, int max_large_cq, cudaStream_t s);
+                const int32_t* work_small, int64_t n_small, const int32_t* work_large, const AcaClass* cls,
+                int n_cls, int max_small_cq, cudaStream_t s);
 
 // Tensor-core (tcgen05) MLP paths (hh_tcmlp.cu): near field in HH_BF16 mode
 // (work = target leaves) and K(r) for a list of separations.
