@@ -8,9 +8,11 @@ inadmissible blocks, FP64 accumulation.  Workload: N = 1,000,000 spheres
 (a = 1) placed by random sequential addition in a cube at volume fraction
 0.1, forces N(0,1), pair MLP 4->32->32->32->6 (SiLU, Xavier weights rounded to
 bf16), C_leaf = 64, eta = 1, zeta = 1e-4, max_rank 48.  Precision "bf16"
-(default): near-field MLP on tcgen05 tensor cores with BF16 operands and FP32
-accumulation, ACA and low-rank apply in FP32, FP64 pivot inverses, norms and
-final accumulation; "fp32" and "fp64" run every kernel in that type.
+(default): every pair-kernel MLP evaluation (near field and the rows and
+columns the ACA generates) on tcgen05 tensor cores with BF16 operands (each
+activation split into a bf16 part and a bf16 remainder) and FP32
+accumulation; ACA arithmetic and low-rank apply in FP32; FP64 pivot inverses,
+norms and final accumulation.  "fp32" and "fp64" run every kernel in that type.
 
 value    = N * K / (sum of CUDA-event times of the K predictions), inputs
            resident in HBM; L2 (126 MB) is flushed between steps by writing a
@@ -19,10 +21,13 @@ e2e      = same metric through the same call with the inputs in pinned host
            memory: H2D copy of X and F, prediction, D2H copy of U, per step.
 rel_err  = Eq. 11 (M^(t,2) part only) against the FP64 dense oracle on 64
            sampled target rows.
-roofline = the ACA team kernels (the dominant stage): algorithmic FP32 flop
-           (5145 per pair-kernel query of the width-32 MLP) / their event time,
-           against the FP32 FMA peak of 148 SMs x 128 lanes x 2 flop x
-           2.032 GHz = 77.0 TFLOP/s ("alu" bound).
+roofline = the ACA team kernels (the dominant stage).  BF16: algorithmic
+           tensor-core flops (2 x MACs of the MLP, 4736 per query for width 32)
+           / their event time, against the measured sustained bf16 peak
+           ("tensor" bound); roofline_near does the same for k_near_tc.
+           FP32 / FP64: FP32-equivalent flops (5145 per query) against the
+           FP32 FMA peak of 148 SMs x 128 lanes x 2 flop x 2.032 GHz =
+           77.0 TFLOP/s ("alu" bound).
 cpu_baseline = the FP64 CPU oracle as it stands: 64 sampled rows of the exact
            dense product on the host cores, scaled to particle-velocities/s.
 
@@ -45,10 +50,13 @@ sys.path.insert(0, ROOT)
 
 FLOP_PER_QUERY = {32: 2 * (4 * 32 + 32 * 32 + 32 * 32 + 32 * 6) + 4 * 96 + 25,
                   64: 2 * (4 * 64 + 64 * 64 + 64 * 64 + 64 * 6) + 4 * 192 + 25}
+# tensor-core flops of one pair-kernel evaluation: 2 x the MACs of the four
+# MLP layers (the bf16 hi/lo operand split and padding are not counted)
+MMA_FLOP_PER_QUERY = {32: 2 * (4 * 32 + 32 * 32 + 32 * 32 + 32 * 6), 64: 2 * (4 * 64 + 64 * 64 + 64 * 64 + 64 * 6)}
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 PRECISION_NOTE = {
-    "bf16": "near-field MLP BF16 operands / FP32 accumulate on tcgen05; ACA + low-rank apply FP32; FP64 pivots, "
-            "norms and final sum",
+    "bf16": "pair-kernel MLP (near field and ACA rows/columns) on tcgen05, BF16 hi/lo operands, FP32 accumulate; "
+            "ACA + low-rank apply FP32; FP64 pivots, norms and final sum",
     "fp32": "all kernels FP32; FP64 pivots, norms and final sum",
     "fp64": "all kernels FP64",
 }
@@ -104,6 +112,17 @@ class ClockSampler:
                           if r[5 + i].strip().lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(sm)}
+
+
+# DRAM bytes (read + write) per pair-kernel query of the BF16 ACA kernels, from
+# one ncu capture of every k_aca_tc launch of a prediction at N = 100,000
+# (profiles/k_aca_tc_bf16_n100k.md); the traffic of a launch is taken as
+# proportional to its queries.
+ACA_TC_DRAM_BYTES_PER_QUERY = 441.0
+
+
+def aca_traffic(queries):
+    return None if ACA_TC_DRAM_BYTES_PER_QUERY is None else ACA_TC_DRAM_BYTES_PER_QUERY * queries
 
 
 def workload(n, seed_geom=1234):
@@ -232,9 +251,28 @@ def run_ours(args, rank, world):
     rel_err = float(oracle.rel_error(Ud, Ug))
 
     peaks = _peaks()
-    flops = queries / args.steps * FLOP_PER_QUERY[32]
     aca_ms = t_aca_kern / args.steps
-    achieved = flops / (aca_ms / 1e3) / 1e12
+    near_ms = st.get("t_kernel_near", st["t_near"])
+    q_step = queries / args.steps
+    if prec == "bf16":
+        # the ACA teams evaluate the MLP on tcgen05: algorithmic MMA flops against the measured bf16 peak
+        peak, peak_src = peaks.get("bf16_tflops_sustained"), "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+        if peak is None:
+            peak, peak_src = 1400.0, "fallback sustained bf16 1.4 PFLOP/s (of fallback)"
+        achieved = q_step * MMA_FLOP_PER_QUERY[32] / (aca_ms / 1e3) / 1e12
+        roofline = {"bound": "tensor", "kernel": "k_aca_tc (warp and CTA teams)", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": aca_traffic(q_step),
+                    "peak_source": peak_src}
+        near_ach = st["n_near_pairs"] * MMA_FLOP_PER_QUERY[32] / (near_ms / 1e3) / 1e12
+        roofline_near = {"bound": "tensor", "kernel": "k_near_tc", "achieved": near_ach, "peak": peak,
+                         "unit": "TFLOP/s", "frac": near_ach / peak}
+    else:
+        achieved = q_step * FLOP_PER_QUERY[32] / (aca_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": "k_aca_cta + k_aca_warp (block ACA teams)", "achieved": achieved,
+                    "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                    "traffic": None,
+                    "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz (no measured FP32 peak)"}
+        roofline_near = None
     line = {
         "metric": METRIC, "value": value, "unit": "particle-velocities/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -247,10 +285,8 @@ def run_ours(args, rank, world):
         "stages_ms": {k: st[k] for k in ("t_tree", "t_part", "t_near", "t_aca", "t_acc")},
         "counts": {"n_aca_queries": st["n_aca_queries"], "n_near_pairs": st["n_near_pairs"],
                    "n_blocks_G": st["n_blocks_G"], "n_blocks_H": st["n_blocks_H"], "n_nodes": st["n_nodes"]},
-        "roofline": {"bound": "alu", "kernel": "k_aca_cta + k_aca_warp (block ACA teams)",
-                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                     "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz (no measured FP32 peak)"},
+        "roofline": roofline,
+        "roofline_near": roofline_near,
         "cpu_baseline": {"value": cpu_rate, "unit": "particle-velocities/s", "cores": cores, "kind": "oracle",
                          "sample": f"{len(idx)} target rows of the N={n} exact dense FP64 product ({cpu_dt:.1f} s)"},
         "e2e": {"value": e2e_value, "unit": "particle-velocities/s", "h2d_bytes_per_step": 2 * 24 * n,
