@@ -348,3 +348,61 @@ class HMatrix(_Owned):
         self.ctx._check(lib().hh_export_aca(self._h, ranks.ctypes.data_as(_P), pI.ctypes.data_as(_P),
                                             pJ.ctypes.data_as(_P), None, None), "hh_export_aca")
         return ranks, pI, pJ
+
+
+def _width_of(n_theta: int) -> int:
+    # 4W + W + 2 (W^2 + W) + 6W + 6 parameters (Eq. 4 MLP 4 -> W -> W -> W -> 6)
+    for w in (32, 64):
+        if 2 * w * w + 13 * w + 6 == n_theta:
+            return w
+    raise ValueError(f"theta has {n_theta} entries: not a 4-W-W-W-6 MLP with W in (32, 64)")
+
+
+_HMATVEC = None
+
+
+def _hmatvec_class():
+    global _HMATVEC
+    if _HMATVEC is not None:
+        return _HMATVEC
+    import torch
+
+    class HMatvec(torch.autograd.Function):
+        """U = alpha_1 F + M_H(X; theta) F through the C-ABI, with the hand-written
+        adjoint hh_matvec_backward as its backward (tree, partition and ACA pivots
+        frozen at the forward's X)."""
+
+        @staticmethod
+        def forward(ctx, X, F, theta, context, params):
+            context.set_mlp(theta.detach(), _width_of(theta.numel()))
+            Xd = X.detach().contiguous()
+            Fd = F.detach().to(torch.float64).contiguous()
+            t = context.build_tree(Xd, params)
+            b = context.partition(t, params)
+            h = context.aca(t, b, params)
+            U = context.matvec(h, Fd)
+            ctx.context, ctx.h, ctx.keep = context, h, (t, b)
+            ctx.theta_dtype, ctx.n_theta = theta.dtype, theta.numel()
+            ctx.save_for_backward(Fd)
+            return U
+
+        @staticmethod
+        def backward(ctx, gU):
+            (Fd,) = ctx.saved_tensors
+            gU = gU.detach().to(torch.float64).contiguous()
+            need_x, need_f, need_t = ctx.needs_input_grad[:3]
+            gF = torch.empty_like(Fd) if need_f else None
+            gX = torch.zeros_like(Fd) if need_x else None
+            gT = torch.zeros(ctx.n_theta, dtype=torch.float32, device=Fd.device) if need_t else None
+            if need_x or need_f or need_t:
+                ctx.context.matvec_backward(ctx.h, gU, Fd, gF=gF, gX=gX, gtheta=gT)
+            return gX, gF, (gT.to(ctx.theta_dtype) if gT is not None else None), None, None
+
+    _HMATVEC = HMatvec
+    return HMatvec
+
+
+def hmatvec(X, F, theta, context: "Context", params: CParams):
+    """Differentiable U = alpha_1 F + M_H(X; theta) F (torch.autograd): gradients
+    with respect to X, F and theta come from hh_matvec_backward."""
+    return _hmatvec_class().apply(X, F, theta, context, params)

@@ -169,3 +169,24 @@ def test_width64_gradient():
     gX, gT = gX.cpu().numpy(), gT.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(gX - gXo) <= 1e-4 * np.linalg.norm(gXo)
     assert np.linalg.norm(gT - gTo) <= 1e-4 * np.linalg.norm(gTo)
+
+
+def test_autograd_function_matches_direct_calls(ctx):
+    n = 1500
+    X0 = hh_synth.rsa_cube(n, 0.1, seed=47)
+    F0, W = hh_synth.forces(n, 13), hh_synth.forces(n, 14)
+    p = hh.Params(precision="fp64")
+    X = cuda(X0).requires_grad_(True)
+    F = cuda(F0).requires_grad_(True)
+    th = torch.as_tensor(THETA, dtype=torch.float32).cuda().requires_grad_(True)
+    c = hh.Context()
+    U = hh.hmatvec(X, F, th, c, p)
+    L = (U * cuda(W)).sum()
+    L.backward()
+    gF, gX, gT, _ = grads(ctx, X0, F0, W, p)
+    assert np.array_equal(F.grad.cpu().numpy(), gF)       # the transposed product is deterministic
+    # dL/dX and dL/dtheta are summed with FP64 atomics: equal up to summation order
+    assert np.abs(X.grad.cpu().numpy() - gX).max() <= 1e-12 * np.abs(gX).max()
+    assert np.abs(th.grad.cpu().numpy().astype(np.float64) - gT).max() <= 1e-6 * np.abs(gT).max()
+    Ud, _ = loss(ctx, X0, F0, W, p)
+    assert float(L) == pytest.approx(Ud, rel=1e-14)
