@@ -90,6 +90,7 @@ __device__ void aca_block(const AcaArgs<R>& A, const Team& tm, S& sm, const R* t
             tm.sync();
             R best = (R)-1;
             int barg = -1;
+            R snu = 0, scr = 0;   // stopping-test terms of the row pass
 #pragma unroll 1
             for (int i = 0; i < ROWS; ++i) {
                 const int x = tid + SIZE * i;
@@ -97,14 +98,20 @@ __device__ void aca_block(const AcaArgs<R>& A, const Team& tm, S& sm, const R* t
                 R rx, ry, rz, K[9];
                 sep<R>(A.Xs, pass == 0 ? t0 + x : t0 + bi, pass == 0 ? s0 + j : s0 + x, rx, ry, rz);
                 pair_block<R, KIND>(th, A.pp, rx, ry, rz, K, hs);
+                R V[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
                 for (int p = 0; p < k; ++p) {
                     R v[9], t9[9];
                     ld9(fac + (int64_t)p * 9 * nx, nx, x, v);
-                    if (pass == 0) mm3(v, piv + 9 * p, t9);   // C_p(m) Q_p(j_k)
-                    else mm3(piv + 9 * p, v, t9);             // C_p(i_k) Q_p(n)
+                    if (pass == 0) {
+                        mm3(v, piv + 9 * p, t9);   // C_p(m) Q_p(j_k)
+                    } else {
+                        mm3(piv + 9 * p, v, t9);   // C_p(i_k) Q_p(n)
+                        add_AtB(V, sm.A + 9 * p, v);
+                    }
 #pragma unroll
                     for (int e = 0; e < 9; ++e) K[e] -= t9[e];
                 }
+                if (pass == 1) row_terms(sm.A + 9 * k, K, V, snu, scr);
                 st9(line, nx, x, K);
                 const bool used = pass == 0 ? is_used(usedR, fR, i, x) : is_used(usedC, fC, i, x);
                 if (!used) {
@@ -117,7 +124,7 @@ __device__ void aca_block(const AcaArgs<R>& A, const Team& tm, S& sm, const R* t
                 bj = barg;
                 tm.sync();
                 double nu2, cross;
-                gram_rows<R>(tm, sm, Qs, q, k, nu2, cross);
+                team_sum2(tm, sm, snu, scr, nu2, cross);
                 if (tid == 0) {
                     lam2 = lam2 + nu2 + 2.0 * cross;
                     sm.stop = (nu2 <= A.eps2 * lam2) || (bj < 0);

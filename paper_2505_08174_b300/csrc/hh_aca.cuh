@@ -185,36 +185,39 @@ __device__ void gram_cols(const Team& tm, S& sm, const R* Cs, int c, int k)
     }
 }
 
-// nu^2 = tr(A_kk B_kk) and cross = sum_{p<k} tr(A_pk B_kp), B_kp = sum_n q_k(n) q_p(n)^T.
-// tr(A B) is linear in B, so each thread adds
-//   tr(A_pk q_k(n) q_p(n)^T) = <A_pk q_k(n), q_p(n)>_F
-// over its own columns n and only two scalars are reduced across the team.
-// Thread 0 receives the sums (FP64).
-template <typename R, class Team, class S>
-__device__ void gram_rows(const Team& tm, S& sm, const R* Qs, int q, int k, double& nu2, double& cross)
+// Stopping-test terms of Eq. 10 with 3x3 Grams, gathered while the row
+// residual is formed: nu^2 = tr(A_kk B_kk) and cross = sum_{p<k} tr(A_pk
+// B_kp), B_kp = sum_n q_k(n) q_p(n)^T.  tr(A B) is linear in B and
+//   tr(A_pk q_k(n) q_p(n)^T) = <A_pk q_k(n), q_p(n)>_F = <q_k(n), A_pk^T q_p(n)>_F,
+// so the thread that forms q_k(n) keeps V(n) = sum_{p<k} A_pk^T Q_p(n) from
+// the same loads of Q_p(n) as the residual update, and adds <A_kk q, q> and
+// <q, V> to its running sums (no second pass over the factors).
+template <typename R>
+__device__ __forceinline__ void add_AtB(R* V, const R* A, const R* B)   // V += A^T B
 {
-    constexpr int SIZE = Team::SIZE;
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+        for (int w = 0; w < 3; ++w) V[3 * u + w] += A[u] * B[w] + A[3 + u] * B[3 + w] + A[6 + u] * B[6 + w];
+}
+
+template <typename R>
+__device__ __forceinline__ void row_terms(const R* A_kk, const R* q, const R* V, R& snu, R& scr)
+{
+    R T[9];
+    mm3(A_kk, q, T);
+    R d = 0, x = 0;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) { d += T[e] * q[e]; x += q[e] * V[e]; }
+    snu += d;
+    scr += x;
+}
+
+// Team sums (FP64) of the two per-thread terms; thread 0 receives them.
+template <typename R, class Team, class S>
+__device__ void team_sum2(const Team& tm, S& sm, R snu, R scr, double& nu2, double& cross)
+{
     const int tid = tm.tid(), lane = threadIdx.x & 31;
-    const R* Qk = Qs + (int64_t)k * 9 * q;
-    R snu = 0, scr = 0;
-    for (int n = tid; n < q; n += SIZE) {
-        R qk[9];
-        ld9(Qk, q, n, qk);
-        for (int p = 0; p <= k; ++p) {
-            R qp[9], T[9];
-            if (p == k) {
-#pragma unroll
-                for (int e = 0; e < 9; ++e) qp[e] = qk[e];
-            } else {
-                ld9(Qs + (int64_t)p * 9 * q, q, n, qp);
-            }
-            mm3(sm.A + 9 * p, qk, T);
-            R d = 0;
-#pragma unroll
-            for (int e = 0; e < 9; ++e) d += T[e] * qp[e];
-            if (p == k) snu += d; else scr += d;
-        }
-    }
     double a = warp_sum((double)snu), b = warp_sum((double)scr);
     if constexpr (Team::NW > 1) {
         if (lane == 0) { sm.red[0][tm.warp()] = a; sm.red[1][tm.warp()] = b; }
@@ -223,6 +226,7 @@ __device__ void gram_rows(const Team& tm, S& sm, const R* Qs, int q, int k, doub
             a = 0.0; b = 0.0;
             for (int w = 0; w < Team::NW; ++w) { a += sm.red[0][w]; b += sm.red[1][w]; }
         }
+        tm.sync();
     }
     nu2 = a;
     cross = b;

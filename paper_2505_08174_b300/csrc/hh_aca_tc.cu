@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
     double lam2 = 0.0;
     float best = -1.f;
     int barg = -1;
+    float snu = 0.f, scr = 0.f;      // stopping-test terms of the current row pass
     uint32_t usedR = 0, usedC = 0;   // warp team: bit i <-> row / column tid + 32 i
     float* Cs = ws;
     float* Qs = ws;
@@ -230,14 +231,20 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
             K[6] = o[4] * id; K[7] = o[5] * id; K[8] = o[2] * id;
             float* fac = pass == 0 ? Cs : Qs;
             const float* piv = pass == 0 ? sm.qj : sm.ci;
+            float V[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             for (int p = 0; p < k; ++p) {
                 float v[9], t9[9];
                 ld9(fac + (int64_t)p * 9 * nx, nx, x, v);
-                if (pass == 0) mm3(v, piv + 9 * p, t9);   // C_p(m) Q_p(j_k)
-                else mm3(piv + 9 * p, v, t9);             // C_p(i_k) Q_p(n)
+                if (pass == 0) {
+                    mm3(v, piv + 9 * p, t9);   // C_p(m) Q_p(j_k)
+                } else {
+                    mm3(piv + 9 * p, v, t9);   // C_p(i_k) Q_p(n)
+                    add_AtB(V, sm.A + 9 * p, v);
+                }
 #pragma unroll
                 for (int e = 0; e < 9; ++e) K[e] -= t9[e];
             }
+            if (pass == 1) row_terms(sm.A + 9 * k, K, V, snu, scr);
             st9(fac + (int64_t)k * 9 * nx, nx, x, K);
             const int i = x0 / SIZE;
             const bool used = pass == 0 ? is_used(usedR, fR, i, x) : is_used(usedC, fC, i, x);
@@ -317,7 +324,7 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
             }
             tm.sync();
             gram_cols<float>(tm, sm, Cs, c, k);
-            pass = 1; x0 = 0; best = -1.f; barg = -1;
+            pass = 1; x0 = 0; best = -1.f; barg = -1; snu = 0.f; scr = 0.f;
             for (int idx = tid; idx < k * 9; idx += SIZE) sm.ci[idx] = Cs[(int64_t)idx * c + bi];
             tm.sync();
         } else {
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
             const int bj = barg;
             tm.sync();
             double nu2, cross;
-            gram_rows<float>(tm, sm, Qs, q, k, nu2, cross);
+            team_sum2(tm, sm, snu, scr, nu2, cross);
             if (tid == 0) {
                 lam2 = lam2 + nu2 + 2.0 * cross;
                 sm.stop = (nu2 <= A.eps2 * lam2) || (bj < 0);
