@@ -16,7 +16,7 @@ struct alignas(128) NearSmem {
 
 // ---- pair evaluation: K(r) for a list of separations --------------------------
 template <int W>
-__global__ void __launch_bounds__(TC_T, 1) k_eval_pairs_tc(const double* __restrict__ r, int64_t n,
+__global__ void __launch_bounds__(TC_T, 4) k_eval_pairs_tc(const double* __restrict__ r, int64_t n,
                                                           const float* __restrict__ th, float a,
                                                           double* __restrict__ K, unsigned* status)
 {
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(TC_T, 1) k_eval_pairs_tc(const double* __restr
 // the MLP, each row's contribution K F_n goes to shared memory and thread m
 // adds the rows of its target in increasing order (bit-reproducible).
 template <int W>
-__global__ void __launch_bounds__(TC_T, 1) k_near_tc(const double* __restrict__ Xs, const double* __restrict__ Fs,
+__global__ void __launch_bounds__(TC_T, 4) k_near_tc(const double* __restrict__ Xs, const double* __restrict__ Fs,
                                                     const int32_t* __restrict__ PH, const int64_t* __restrict__ rowH,
                                                     const int32_t* __restrict__ work, int64_t n_work,
                                                     const int32_t* __restrict__ nbeg, const int32_t* __restrict__ nend,

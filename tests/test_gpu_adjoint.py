@@ -189,4 +189,4 @@ def test_autograd_function_matches_direct_calls(ctx):
     assert np.abs(X.grad.cpu().numpy() - gX).max() <= 1e-12 * np.abs(gX).max()
     assert np.abs(th.grad.cpu().numpy().astype(np.float64) - gT).max() <= 1e-6 * np.abs(gT).max()
     Ud, _ = loss(ctx, X0, F0, W, p)
-    assert float(L) == pytest.approx(Ud, rel=1e-14)
+    assert float(L.detach()) == pytest.approx(Ud, rel=1e-14)
