@@ -42,14 +42,17 @@ struct AcaArgs {
     unsigned long long* n_queries;
 };
 
-template <typename R>
+// Shared state of one team; MR bounds the rank (max_rank <= MR).
+template <typename R, int MR = MAXR>
 struct alignas(16) TeamSmem {
-    R qj[MAXR * 9];        // Q_p(j_k), p < k
-    R ci[MAXR * 9];        // C_p(i_k), p < k
-    R A[(MAXR + 1) * 9];   // A_pk, p <= k
+    union {
+        R qj[MR * 9];      // Q_p(j_k), p < k (rank loop)
+        R tv[MR * 3];      // t_p = sum_n Q_p(n) F(n) (fused apply, after the loop)
+    };
+    R ci[MR * 9];          // C_p(i_k), p < k
+    R A[(MR + 1) * 9];     // A_pk, p <= k
     double red[2][8];      // per-warp partials of nu^2 and the cross term
     R Pi[9];
-    R tv[MAXR * 3];
     double rv[8];
     int ri[8];
     int flag, stop;

@@ -24,10 +24,10 @@
 
 namespace {
 
-template <int W, class Team>
+template <int W, class Team, int MR>
 struct alignas(128) AcaTcSmem {
     TcCore<W> tc;
-    TeamSmem<float> team[TC_T / Team::SIZE];
+    TeamSmem<float, MR> team[TC_T / Team::SIZE];
     int blk[TC_T / Team::SIZE];
     uint64_t mbw[4];      // warp teams: one MMA barrier per warp
     uint32_t pend[4];
@@ -67,7 +67,7 @@ __device__ void aca_tc_teardown(S& sm)
     if (threadIdx.x < 32) tmem_dealloc(sm.tc.tmem, aca_tmem_cols<W>());
 }
 
-template <int W, class Team>
+template <int W, class Team, int MR>
 __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const float* __restrict__ th_packed, int mode)
 {
     constexpr int NT = TC_T / Team::SIZE;
@@ -75,12 +75,12 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
     constexpr bool REG = Team::REG_FLAGS;
     constexpr bool CTA = NT == 1;   // one 128-thread team per CTA, else 4 warp teams
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    AcaTcSmem<W, Team>& S = *reinterpret_cast<AcaTcSmem<W, Team>*>(smem_raw);
+    AcaTcSmem<W, Team, MR>& S = *reinterpret_cast<AcaTcSmem<W, Team, MR>*>(smem_raw);
     aca_tc_setup<W>(S, th_packed);
     const Team tm;
     const int team = threadIdx.x / SIZE;
     const int tid = tm.tid();
-    TeamSmem<float>& sm = S.team[team];
+    TeamSmem<float, MR>& sm = S.team[team];
     float* const ws = A.scratch + ((int64_t)blockIdx.x * NT + team) * A.team_stride;
     const float a = (float)A.pp.a;
     const int warp = threadIdx.x >> 5;   // TMEM quadrant, accumulator columns and mbarrier of this warp
@@ -353,13 +353,22 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
     aca_tc_teardown<W>(S);
 }
 
+template <int W, class Team, int MR>
+void launch_tc_mr(hh_ctx* ctx, const AcaArgs<float>& A, int64_t grid, int mode, cudaStream_t s)
+{
+    const size_t smem = sizeof(AcaTcSmem<W, Team, MR>) + 128;
+    HH_CUDA(cudaFuncSetAttribute(k_aca_tc<W, Team, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_aca_tc<W, Team, MR><<<(unsigned)grid, TC_T, smem, s>>>(A, ctx->theta32, mode);
+    HH_CHECK_LAUNCH();
+}
+
+// Shared state sized for max_rank <= 48 (the default) when possible: it
+// keeps a CTA under 56 KB, so four CTAs share an SM.
 template <int W, class Team>
 void launch_tc(hh_ctx* ctx, const AcaArgs<float>& A, int64_t grid, int mode, cudaStream_t s)
 {
-    const size_t smem = sizeof(AcaTcSmem<W, Team>) + 128;
-    HH_CUDA(cudaFuncSetAttribute(k_aca_tc<W, Team>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_aca_tc<W, Team><<<(unsigned)grid, TC_T, smem, s>>>(A, ctx->theta32, mode);
-    HH_CHECK_LAUNCH();
+    if (A.max_rank <= 48) launch_tc_mr<W, Team, 48>(ctx, A, grid, mode, s);
+    else launch_tc_mr<W, Team, MAXR>(ctx, A, grid, mode, s);
 }
 
 }  // namespace

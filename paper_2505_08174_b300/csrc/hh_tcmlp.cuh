@@ -7,9 +7,9 @@
 //   A1 [128 x 16]  = [f_hi(4) | f_lo(4) | 1 | 0...]  (f = [r/|r|, a/|r|])
 //   L1: D = A1 B1^T,  B1 [W x 16] = [W1 | W1 | b1 | 0]          (1 MMA, N = W)
 //   epilogue: h = SiLU(D) -> AH [128 x 2W] = [h_hi | h_lo] (bf16)
-//   L2: D = AH B2^T,  B2 [W x 2W] = [W2 | W2]                    (2W/16 MMAs)
+//   L2: D = AH_hi W2^T + AH_lo W2^T,  B2 [W x W] = W2           (2W/16 MMAs)
 //   epilogue: h = SiLU(D + b2) -> AH;   L3 likewise with W3, b3
-//   L4: D = AH B4^T,  B4 [16 x 2W] = [W4 | W4] padded to 16 rows; o = D + b4
+//   L4: D = AH_hi W4^T + AH_lo W4^T,  B4 [16 x W] = W4 padded to 16 rows; o = D + b4
 // Splitting every activation into a bf16 "hi" part and a bf16 remainder keeps
 // ~16 significant bits of each activation; the weights are exactly bf16 (the
 // canonical network), so the products are exact and only the FP32
@@ -33,9 +33,9 @@ struct alignas(128) TcCore {
     __nv_bfloat16 A1[TC_T * 16];
     __nv_bfloat16 AH[TC_T * 2 * W];
     __nv_bfloat16 B1[W * 16];
-    __nv_bfloat16 B2[W * 2 * W];
-    __nv_bfloat16 B3[W * 2 * W];
-    __nv_bfloat16 B4[16 * 2 * W];
+    __nv_bfloat16 B2[W * W];    // applied to both halves of AH (two MMAs per K chunk pair)
+    __nv_bfloat16 B3[W * W];
+    __nv_bfloat16 B4[16 * W];
     float b2[W], b3[W], b4[16];
     uint64_t mbar;
     uint32_t tmem;
@@ -98,15 +98,15 @@ __device__ void tc_load_weights(TcCore<W>& sm, const float* __restrict__ th)
         float v = k < 4 ? W1[4 * j + k] : (k < 8 ? W1[4 * j + k - 4] : (k == 8 ? b1[j] : 0.f));
         *reinterpret_cast<__nv_bfloat16*>(B1 + tc_elem_offset(j, k, 16)) = __float2bfloat16_rn(v);
     }
-    for (int x = threadIdx.x; x < W * 2 * W; x += blockDim.x) {
-        const int j = x / (2 * W), k = x % (2 * W), kk = k % W;
-        *reinterpret_cast<__nv_bfloat16*>(B2 + tc_elem_offset(j, k, 2 * W)) = __float2bfloat16_rn(W2[W * j + kk]);
-        *reinterpret_cast<__nv_bfloat16*>(B3 + tc_elem_offset(j, k, 2 * W)) = __float2bfloat16_rn(W3[W * j + kk]);
+    for (int x = threadIdx.x; x < W * W; x += blockDim.x) {
+        const int j = x / W, k = x % W;
+        *reinterpret_cast<__nv_bfloat16*>(B2 + tc_elem_offset(j, k, W)) = __float2bfloat16_rn(W2[W * j + k]);
+        *reinterpret_cast<__nv_bfloat16*>(B3 + tc_elem_offset(j, k, W)) = __float2bfloat16_rn(W3[W * j + k]);
     }
-    for (int x = threadIdx.x; x < 16 * 2 * W; x += blockDim.x) {
-        const int j = x / (2 * W), k = x % (2 * W), kk = k % W;
-        float v = j < 6 ? W4[W * j + kk] : 0.f;
-        *reinterpret_cast<__nv_bfloat16*>(B4 + tc_elem_offset(j, k, 2 * W)) = __float2bfloat16_rn(v);
+    for (int x = threadIdx.x; x < 16 * W; x += blockDim.x) {
+        const int j = x / W, k = x % W;
+        float v = j < 6 ? W4[W * j + k] : 0.f;
+        *reinterpret_cast<__nv_bfloat16*>(B4 + tc_elem_offset(j, k, W)) = __float2bfloat16_rn(v);
     }
     for (int j = threadIdx.x; j < W; j += blockDim.x) { sm.b2[j] = b2[j]; sm.b3[j] = b3[j]; }
     for (int j = threadIdx.x; j < 16; j += blockDim.x) sm.b4[j] = j < 6 ? b4[j] : 0.f;
@@ -148,16 +148,20 @@ __device__ __forceinline__ bool tc_wait(TcCore<W>& sm, uint32_t& phase, unsigned
     return true;
 }
 
-// Issue one layer: D[tmem] = A (128 x K) * B (N x K)^T, K = 16 * nk.
-__device__ __forceinline__ void tc_issue_layer(uint32_t tmem, const void* A, const void* B, int K, int N,
+// Issue one layer: D[tmem] = sum over the K/16 chunks kc of A(:, kc) B(:, kc
+// mod KB/16)^T -- A is 128 x K, B is N x KB with KB dividing K, so B is
+// applied to each KB-wide slice of A (the bf16 hi and lo halves of the
+// activations share one copy of the weights).
+__device__ __forceinline__ void tc_issue_layer(uint32_t tmem, const void* A, const void* B, int K, int KB, int N,
                                                uint64_t* mbar)
 {
     const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
-    const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+    const uint32_t sbo_a = (uint32_t)(K / 8) * 128u, sbo_b = (uint32_t)(KB / 8) * 128u;
     const uint32_t idesc = tc_idesc_bf16(128, N);
+    const int nb = KB / 16;
     for (int kc = 0; kc < K / 16; ++kc) {
-        const uint64_t da = tc_smem_desc(a0 + 256u * kc, 128u, sbo);
-        const uint64_t db = tc_smem_desc(b0 + 256u * kc, 128u, sbo);
+        const uint64_t da = tc_smem_desc(a0 + 256u * kc, 128u, sbo_a);
+        const uint64_t db = tc_smem_desc(b0 + 256u * (kc % nb), 128u, sbo_b);
         tc_mma_bf16(tmem, da, db, idesc, kc > 0 ? 1u : 0u);
     }
     tc_commit(mbar);
@@ -204,7 +208,7 @@ __device__ bool tc_mlp_tile(TcCore<W>& sm, uint32_t& phase, unsigned* status, fl
     __syncthreads();
     if (t == 0) {
         tc_fence_after();
-        tc_issue_layer(sm.tmem, sm.A1, sm.B1, 16, W, &sm.mbar);
+        tc_issue_layer(sm.tmem, sm.A1, sm.B1, 16, 16, W, &sm.mbar);
     }
     if (!tc_wait(sm, phase, status)) return false;
     tc_hidden_epilogue<W>(sm, trow, nullptr, t);
@@ -216,7 +220,7 @@ __device__ bool tc_mlp_tile(TcCore<W>& sm, uint32_t& phase, unsigned* status, fl
         __syncthreads();
         if (t == 0) {
             tc_fence_after();
-            tc_issue_layer(sm.tmem, sm.AH, l == 0 ? sm.B2 : sm.B3, 2 * W, W, &sm.mbar);
+            tc_issue_layer(sm.tmem, sm.AH, l == 0 ? sm.B2 : sm.B3, 2 * W, W, W, &sm.mbar);
         }
         if (!tc_wait(sm, phase, status)) return false;
         tc_hidden_epilogue<W>(sm, trow, l == 0 ? sm.b2 : sm.b3, t);
@@ -227,7 +231,7 @@ __device__ bool tc_mlp_tile(TcCore<W>& sm, uint32_t& phase, unsigned* status, fl
     __syncthreads();
     if (t == 0) {
         tc_fence_after();
-        tc_issue_layer(sm.tmem, sm.AH, sm.B4, 2 * W, 16, &sm.mbar);
+        tc_issue_layer(sm.tmem, sm.AH, sm.B4, 2 * W, W, 16, &sm.mbar);
     }
     if (!tc_wait(sm, phase, status)) return false;
     float v[16];
@@ -313,8 +317,9 @@ __device__ bool tcw_mlp_rows(TcCore<W>& sm, TcWarp& w, unsigned* status, float o
         __syncwarp();
         if (lane == 0) {
             tc_fence_after();
-            if (l == 0) tc_issue_layer(w.tcol, sm.A1, sm.B1, 16, W, w.mbar);
-            else tc_issue_layer(w.tcol, sm.AH, l == 1 ? sm.B2 : (l == 2 ? sm.B3 : sm.B4), 2 * W, l == 3 ? 16 : W, w.mbar);
+            if (l == 0) tc_issue_layer(w.tcol, sm.A1, sm.B1, 16, 16, W, w.mbar);
+            else tc_issue_layer(w.tcol, sm.AH, l == 1 ? sm.B2 : (l == 2 ? sm.B3 : sm.B4), 2 * W, W, l == 3 ? 16 : W,
+                                w.mbar);
         }
         if (!tcw_wait(w, status)) return false;
         if (l < 3) tc_hidden_epilogue<W>(sm, trow, l == 0 ? nullptr : (l == 1 ? sm.b2 : sm.b3), t);
