@@ -32,6 +32,9 @@ PINS = {
     "hmatvec": "equals the dense product when nothing is admissible; eps_r <= zeta; decreasing in zeta",
     "grad": "central finite differences of the dense product; gF against the dense matrix transpose",
     "train": "finite differences of the Eq. 5 loss; Adam step against its closed form",
+    "mlp_gen": "equals the pinned 4 -> w -> w -> w -> 6 pair MLP for those sizes",
+    "short_range": "constant-output networks against a distance-matrix formulation (numpy); hand-derived "
+                   "3-particle cliques; translation invariance; permutation equivariance",
 }
 
 
@@ -97,6 +100,8 @@ def _declare(L):
         "or_hmatvec": (_I, [_I, _P, _P, _P, _I, _D, _D, _I, _I, ctypes.c_uint64, _I, _P, _P, _P, _P, _P, _I64]),
         "or_rel_error": (_D, [_I64, _P, _P]),
         "or_num_threads": (_I, []),
+        "or_mlp_gen": (None, [_P, _I, _I, _I, _P, _P]),
+        "or_short_range": (None, [_I, _P, _P, _P, _I, _P, _I, _D, _D, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -312,3 +317,23 @@ def rel_error(ref, approx):
 
 def num_threads():
     return lib().or_num_threads()
+
+
+def mlp_gen(theta, n_in, width, n_out, f):
+    """MLP n_in -> width x 3 -> n_out (SiLU), FP64."""
+    th = _f64(theta)
+    f = _f64(f)
+    o = np.zeros(n_out)
+    lib().or_mlp_gen(_ptr(th), n_in, width, n_out, _ptr(f), _ptr(o))
+    return o
+
+
+def short_range(X, F, theta_s=None, ws=32, theta_3=None, w3=32, rcut=5.0, a=1.0):
+    """Short-range terms of Eq. 6 (M^(s,2) + M^(t,3) + M^(s,3)) F for one suspension (FP64)."""
+    X, F = _f64(X), _f64(F)
+    ts = _f64(theta_s) if theta_s is not None else None
+    t3 = _f64(theta_3) if theta_3 is not None else None
+    U = np.zeros_like(X)
+    lib().or_short_range(len(X), _ptr(X), _ptr(F), _ptr(ts), ws, _ptr(t3), w3, float(rcut), float(a), _ptr(U))
+    return U
+

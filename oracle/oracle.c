@@ -22,7 +22,9 @@
  *   - the H-matrix product built from the above;
  *   - the relative error of Eq. 11;
  *   - the analytic gradient of L = sum_i w_i . U_i w.r.t. F, X and theta,
- *     and the training loss of Eq. 5 with its gradient and an Adam step.
+ *     and the training loss of Eq. 5 with its gradient and an Adam step;
+ *   - the short-range terms M^(s,2), M^(t,3), M^(s,3) of Eq. 6 (Eq. 2 with
+ *     the Eq. 4 normalisations) over neighbours within R_cut.
  *
  * Readings of points the paper leaves open are stated where they are used.
  */
@@ -743,6 +745,119 @@ int or_aca_dense(const double *G, int c, int q, double eps, int max_rank, int j1
 {
     or_dense_entry_ctx ctx = {G, q};
     return or_aca_core(or_dense_entry, &ctx, c, q, eps, max_rank, j1, C, Q, I, J, lambda2, flags);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Short-range terms: M^(s,2), M^(t,3), M^(s,3) of Eq. 6                    */
+/* ------------------------------------------------------------------------ */
+
+/* MLP n_in -> w -> w -> w -> n_out, SiLU after each hidden layer, linear
+ * output; parameters packed per layer as W [out, in] then b [out]. */
+void or_mlp_gen(const double *theta, int n_in, int w, int n_out, const double *f, double *o)
+{
+    double h[256], g[256];
+    const double *p = theta;
+    p = or_layer(p, n_in, w, f, h);
+    for (int i = 0; i < w; ++i) h[i] = or_silu(h[i]);
+    p = or_layer(p, w, w, h, g);
+    for (int i = 0; i < w; ++i) g[i] = or_silu(g[i]);
+    p = or_layer(p, w, w, g, h);
+    for (int i = 0; i < w; ++i) h[i] = or_silu(h[i]);
+    or_layer(p, w, n_out, h, o);
+}
+
+/* Neighbour lists N(i) = { j != i : |x_i - x_j| < rcut } by brute force
+ * (CSR: off[n+1], idx in increasing j). */
+static void or_neighbours(int n, const double *X, double rcut, int64_t **off_out, int32_t **idx_out)
+{
+    int64_t *off = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    const double rc2 = rcut * rcut;
+    for (int i = 0; i < n; ++i) {
+        int64_t cnt = 0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = X[3 * i] - X[3 * j], dy = X[3 * i + 1] - X[3 * j + 1], dz = X[3 * i + 2] - X[3 * j + 2];
+            if (dx * dx + dy * dy + dz * dz < rc2) ++cnt;
+        }
+        off[i + 1] = off[i] + cnt;
+    }
+    int32_t *idx = (int32_t *)malloc(sizeof(int32_t) * (size_t)(off[n] > 0 ? off[n] : 1));
+    for (int i = 0; i < n; ++i) {
+        int64_t w = off[i];
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = X[3 * i] - X[3 * j], dy = X[3 * i + 1] - X[3 * j + 1], dz = X[3 * i + 2] - X[3 * j + 2];
+            if (dx * dx + dy * dy + dz * dz < rc2) idx[w++] = j;
+        }
+    }
+    *off_out = off;
+    *idx_out = idx;
+}
+
+/* U_i += sum over the short-range terms of Eq. 2 (Eq. 6: M^(s,2) + M^(t,3)
+ * + M^(s,3)) with the normalisations of Eq. 4, for one suspension of n
+ * particles (added to U, FP64):
+ *   two-body self part, j in N(i), r = x_i - x_j, d = |r|:
+ *     alpha2s = (a/d)^4 / d * S(MLP_s([r/d, a/d]))   applied to F_i;
+ *   three-body, 3-cliques (j, k, i) with i, j in N(k), j != i (k in N(i),
+ *   j in N(k) \ {i}), r_ji = x_j - x_i, r_ki = x_k - x_i, d_jk = |x_j - x_k|:
+ *     o = MLP_3([r_ji/|r_ji|, r_ki/|r_ki|, a/d_jk]) (12 outputs),
+ *     alpha3 = [S(o_0..5), S(o_6..11)] / (d_jk |r_ki|)  applied to [F_i; F_j].
+ * theta_s: MLP 4 -> ws -> ws -> ws -> 6; theta_3: MLP 7 -> w3 -> w3 -> w3 -> 12
+ * (either may be NULL to leave its term out). */
+void or_short_range(int n, const double *X, const double *F, const double *theta_s, int ws, const double *theta_3,
+                    int w3, double rcut, double a, double *U)
+{
+    int64_t *off;
+    int32_t *idx;
+    or_neighbours(n, X, rcut, &off, &idx);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int i = 0; i < n; ++i) {
+        double ui[3] = {0.0, 0.0, 0.0};
+        const double *xi = X + 3 * i, *Fi = F + 3 * i;
+        if (theta_s) {
+            for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+                const int j = idx[e];
+                double r[3] = {xi[0] - X[3 * j], xi[1] - X[3 * j + 1], xi[2] - X[3 * j + 2]};
+                double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+                double f[4] = {r[0] / d, r[1] / d, r[2] / d, a / d};
+                double o[6], S[9];
+                or_mlp_gen(theta_s, 4, ws, 6, f, o);
+                or_sym3(o, S);
+                double q = a / d, c = q * q * q * q / d;
+                for (int u = 0; u < 3; ++u) ui[u] += c * (S[3 * u] * Fi[0] + S[3 * u + 1] * Fi[1] + S[3 * u + 2] * Fi[2]);
+            }
+        }
+        if (theta_3) {
+            for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+                const int k = idx[e];
+                double rki[3] = {X[3 * k] - xi[0], X[3 * k + 1] - xi[1], X[3 * k + 2] - xi[2]};
+                double dki = sqrt(rki[0] * rki[0] + rki[1] * rki[1] + rki[2] * rki[2]);
+                for (int64_t e2 = off[k]; e2 < off[k + 1]; ++e2) {
+                    const int j = idx[e2];
+                    if (j == i) continue;
+                    double rji[3] = {X[3 * j] - xi[0], X[3 * j + 1] - xi[1], X[3 * j + 2] - xi[2]};
+                    double dji = sqrt(rji[0] * rji[0] + rji[1] * rji[1] + rji[2] * rji[2]);
+                    double djk[3] = {X[3 * j] - X[3 * k], X[3 * j + 1] - X[3 * k + 1], X[3 * j + 2] - X[3 * k + 2]};
+                    double dj = sqrt(djk[0] * djk[0] + djk[1] * djk[1] + djk[2] * djk[2]);
+                    double f[7] = {rji[0] / dji, rji[1] / dji, rji[2] / dji, rki[0] / dki, rki[1] / dki, rki[2] / dki,
+                                   a / dj};
+                    double o[12], Ss[9], St[9];
+                    or_mlp_gen(theta_3, 7, w3, 12, f, o);
+                    or_sym3(o, Ss);
+                    or_sym3(o + 6, St);
+                    const double *Fj = F + 3 * j;
+                    double c = 1.0 / (dj * dki);
+                    for (int u = 0; u < 3; ++u)
+                        ui[u] += c * (Ss[3 * u] * Fi[0] + Ss[3 * u + 1] * Fi[1] + Ss[3 * u + 2] * Fi[2] +
+                                      St[3 * u] * Fj[0] + St[3 * u + 1] * Fj[1] + St[3 * u + 2] * Fj[2]);
+                }
+            }
+        }
+        for (int u = 0; u < 3; ++u) U[3 * i + u] += ui[u];
+    }
+    free(off);
+    free(idx);
 }
 
 /* ------------------------------------------------------------------------ */
