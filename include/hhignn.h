@@ -67,6 +67,12 @@ enum { HH_FP64 = 0, HH_FP32 = 1, HH_BF16 = 2 };   /* hh_params.precision */
 enum { HH_MLP = 0, HH_RPY = 1 };                  /* hh_params.kernel    */
 
 /* Parameters of one H-matrix build (Section 3 and Section 4 notation). */
+/* hh_params.flags: add the short-range terms M^(s,2) + M^(t,3) + M^(s,3) of
+ * Eq. 6 (networks and R_cut from hh_set_short_range) in hh_predict and in
+ * hh_matvec (forward only; the transposed product and the adjoint refuse
+ * the flag with HH_ERR_ARG). */
+#define HH_FLAG_SHORT_RANGE 1
+
 typedef struct {
     int32_t leaf_size;   /* C_leaf: a cluster is a leaf iff |tau| < C_leaf (Def. 1); 2..129 */
     double eta;          /* admissibility parameter of Eq. 7 (> 0)                          */
@@ -80,7 +86,7 @@ typedef struct {
     uint64_t seed;       /* seed of the j_1 hash                                            */
     int32_t shard_id;    /* this shard's share of the block work lists                      */
     int32_t n_shards;    /* number of shards (1 = everything)                               */
-    int32_t flags;       /* reserved, 0                                                     */
+    int32_t flags;       /* HH_FLAG_* bits, 0 = none                                        */
 } hh_params;
 
 /* Fills *p with the defaults: leaf 32, eta 1, eps 1e-4, max_rank 48, FP32,
@@ -227,7 +233,34 @@ typedef struct {
     double t_kernel_aca;    /* ms inside the ACA team kernels (CUDA events)   */
     double t_kernel_near;   /* ms inside the near-field kernel (CUDA events)  */
     int64_t n_launches;     /* kernels this library launched in the call      */
+    double t_short;         /* ms of the short-range terms (0 when off)       */
+    int64_t n_short_pairs;  /* neighbour pairs within R_cut (directed)        */
 } hh_stats_t;
+
+/* Short-range networks of Eq. 6 (Eq. 2 with the Eq. 4 normalisations; the
+ * paper trains them on three-particle data, here they are caller-supplied):
+ *   two-body self part  alpha_2^(s)(i, j) = (a/d)^4 / d * S(MLP_s([r/d, a/d])),
+ *                       r = x_i - x_j, d = |r|, applied to F_i;
+ *   three-body          alpha_3 = [S(o_0..5), S(o_6..11)] / (|x_j - x_k| |x_k - x_i|),
+ *                       o = MLP_3([r_ji/|r_ji|, r_ki/|r_ki|, a/|x_j - x_k|]),
+ *                       r_ji = x_j - x_i, r_ki = x_k - x_i, applied to [F_i; F_j],
+ * summed over j in N(i) and over the 3-cliques (j, k, i) with i, j in N(k),
+ * j != i, where N(i) = { j != i : |x_i - x_j| < r_cut } within one
+ * suspension.  S(o) = [[o0,o3,o4],[o3,o1,o5],[o4,o5,o2]].  theta_s_dev:
+ * MLP 4 -> width -> width -> width -> 6, theta_3_dev: MLP 7 -> width x 3 ->
+ * 12, both float32 device arrays packed per layer as W[out, in] then b[out]
+ * (copied; either may be NULL to leave its term out); width 32 or 64;
+ * r_cut > 0.  Positions spanning more than 65535 r_cut per axis in one
+ * suspension make the calls that use them fail with HH_ERR_NUMERIC. */
+hh_status hh_set_short_range(hh_ctx *ctx, const float *theta_s_dev, const float *theta_3_dev, int width,
+                             double r_cut, void *stream);
+
+/* U_dev [N,3] FP64 (caller order) += the short-range terms above for X_dev,
+ * F_dev [N,3] FP64, suspensions given by offsets (host, [batch+1]) as in
+ * hh_predict; p->precision selects FP64 or FP32 arithmetic, p->radius is a.
+ * Asynchronous on stream except for one size query. */
+hh_status hh_short_range(hh_ctx *ctx, const double *X_dev, const double *F_dev, const int64_t *offsets,
+                         int32_t batch, const hh_params *p, void *stream, double *U_dev);
 
 /* Counters of the last hh_predict / hh_aca on ctx. */
 hh_status hh_stats(hh_ctx *ctx, hh_stats_t *out);

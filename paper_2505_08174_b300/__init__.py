@@ -34,7 +34,7 @@ EXPORTS = [
     "hh_partition", "hh_aca", "hh_matvec", "hh_predict", "hh_matvec_backward", "hh_export_tree",
     "hh_export_blocks", "hh_export_aca", "hh_stats", "hh_tree_free", "hh_blocks_free", "hh_hmat_free",
     "hh_aca_block_apply_noalloc", "hh_eval_pairs", "hh_train_loss_grad", "hh_train_step",
-    "hh_set_launch", "hh_get_launch", "hh_autotune",
+    "hh_set_launch", "hh_get_launch", "hh_autotune", "hh_set_short_range", "hh_short_range",
 ]
 
 
@@ -58,7 +58,8 @@ class CStats(ctypes.Structure):
                 ("n_near_pairs", ctypes.c_int64), ("n_aca_queries", ctypes.c_int64),
                 ("n_blocks_G", ctypes.c_int64), ("n_blocks_H", ctypes.c_int64), ("n_nodes", ctypes.c_int64),
                 ("rank_hist", ctypes.c_int64 * 65), ("t_kernel_aca", ctypes.c_double),
-                ("t_kernel_near", ctypes.c_double), ("n_launches", ctypes.c_int64)]
+                ("t_kernel_near", ctypes.c_double), ("n_launches", ctypes.c_int64), ("t_short", ctypes.c_double),
+                ("n_short_pairs", ctypes.c_int64)]
 
 
 class CLaunch(ctypes.Structure):
@@ -105,6 +106,11 @@ def lib():
             "hh_train_loss_grad": (st, [_P, _P, ctypes.c_int, _P, _P, _P, i64, ctypes.c_double, _P, _P, _P]),
             "hh_train_step": (st, [_P, _P, _P, _P, i64, ctypes.c_int, _P, _P, _P, i64, ctypes.c_double,
                                    ctypes.c_double, _P, _P]),
+            "hh_set_launch": (st, [_P, _P]),
+            "hh_get_launch": (st, [_P, _P]),
+            "hh_autotune": (st, [_P, _P, _P, i32, _P, i32, _P, _P]),
+            "hh_set_short_range": (st, [_P, _P, _P, ctypes.c_int, ctypes.c_double, _P]),
+            "hh_short_range": (st, [_P, _P, _P, _P, i32, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -114,8 +120,11 @@ def lib():
     return _lib
 
 
+FLAG_SHORT_RANGE = 1
+
+
 def Params(leaf_size=32, eta=1.0, eps=1e-4, max_rank=48, precision="fp32", kernel="mlp", radius=1.0,
-           viscosity=1.0, j1_rule=0, seed=0, shard_id=0, n_shards=1) -> CParams:
+           viscosity=1.0, j1_rule=0, seed=0, shard_id=0, n_shards=1, short_range=False) -> CParams:
     p = CParams()
     lib().hh_default_params(ctypes.byref(p))
     p.leaf_size, p.eta, p.eps, p.max_rank = leaf_size, eta, eps, max_rank
@@ -123,6 +132,7 @@ def Params(leaf_size=32, eta=1.0, eps=1e-4, max_rank=48, precision="fp32", kerne
     p.kernel = KERNELS[kernel] if isinstance(kernel, str) else kernel
     p.radius, p.viscosity, p.j1_rule, p.seed = radius, viscosity, j1_rule, seed
     p.shard_id, p.n_shards = shard_id, n_shards
+    p.flags = FLAG_SHORT_RANGE if short_range else 0
     return p
 
 
@@ -216,6 +226,26 @@ class Context:
                                         _dptr(U) if U is not None else None, r.shape[0], radius, lr,
                                         _stream(stream), ctypes.byref(loss)), "hh_train_step")
         return loss.value
+
+    # -- short-range terms (Eq. 6: M^(s,2) + M^(t,3) + M^(s,3)) -------------------
+    def set_short_range(self, theta_s, theta_3, width: int, r_cut: float = 5.0, stream=None):
+        import torch
+        dev = f"cuda:{self.device}"
+        ts = None if theta_s is None else torch.as_tensor(theta_s, dtype=torch.float32).to(dev).contiguous()
+        t3 = None if theta_3 is None else torch.as_tensor(theta_3, dtype=torch.float32).to(dev).contiguous()
+        p = lambda t: _dptr(t) if t is not None else None
+        self._check(lib().hh_set_short_range(self._h, p(ts), p(t3), int(width), float(r_cut), _stream(stream)),
+                    "hh_set_short_range")
+
+    def short_range(self, X, F, params: CParams, offsets=None, out=None, stream=None):
+        """U (+)= the short-range terms for X, F (caller order); out is accumulated into when given."""
+        import torch
+        _check_xyz(X, "X"); _check_xyz(F, "F")
+        off = np.asarray([0, X.shape[0]] if offsets is None else offsets, dtype=np.int64)
+        U = torch.zeros_like(X) if out is None else out
+        self._check(lib().hh_short_range(self._h, _dptr(X), _dptr(F), off.ctypes.data_as(_P), len(off) - 1,
+                                         ctypes.byref(params), _stream(stream), _dptr(U)), "hh_short_range")
+        return U
 
     # -- launch shape and autotuner ---------------------------------------------
     def set_launch(self, small_max=0, aca_small_cps=0, aca_large_cps=0, near_cps=0):

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 
 #include <algorithm>
@@ -62,6 +63,9 @@ void check_params(const hh_ctx* ctx, const hh_params* p)
     HH_REQUIRE(p->radius > 0.0 && p->viscosity > 0.0, HH_ERR_ARG, "radius and viscosity must be > 0");
     HH_REQUIRE(p->n_shards >= 1 && p->shard_id >= 0 && p->shard_id < p->n_shards, HH_ERR_ARG, "bad shard");
     HH_REQUIRE(p->j1_rule == 0 || p->j1_rule == 1, HH_ERR_ARG, "j1_rule must be 0 or 1");
+    HH_REQUIRE((p->flags & ~HH_FLAG_SHORT_RANGE) == 0, HH_ERR_ARG, "unknown flags");
+    HH_REQUIRE(!(p->flags & HH_FLAG_SHORT_RANGE) || ctx->sr_width > 0, HH_ERR_ARG,
+               "HH_FLAG_SHORT_RANGE needs hh_set_short_range");
 }
 
 __global__ void k_fill(double* __restrict__ a, int64_t n, double v)
@@ -213,6 +217,10 @@ void hh_destroy(hh_ctx* ctx)
     cudaFree(ctx->theta32);
     cudaFree(ctx->theta32t);
     cudaFree(ctx->theta64);
+    cudaFree(ctx->sr_theta_s32);
+    cudaFree(ctx->sr_theta_332);
+    cudaFree(ctx->sr_theta_s64);
+    cudaFree(ctx->sr_theta_364);
     cudaFree(ctx->d_status);
     cudaFree(ctx->d_counters);
     for (auto& e : ctx->ev)
@@ -386,8 +394,12 @@ hh_status hh_matvec(hh_ctx* ctx, const hh_hmat* h, const double* F_dev, double* 
         const int rb = real_bytes(p);
         double* Fs = dev_alloc_t<double>(3 * t->n, s);
         gather_rows(F_dev, t->perm, t->n, Fs, s);
+        HH_REQUIRE(!(transpose && (p.flags & HH_FLAG_SHORT_RANGE)), HH_ERR_ARG,
+                   "the transposed product does not cover the short-range terms");
         void* y = dev_alloc(rb * 3 * (size_t)t->n, s);
         near_field(ctx, t, b, p, Fs, y, transpose, s);
+        if ((p.flags & HH_FLAG_SHORT_RANGE) && p.shard_id == 0)
+            short_range_add(ctx, t->Xs, Fs, t->n, t->offsets, t->d_offsets, p, y, rb == 8, s);
         int64_t* pofs = dev_alloc_t<int64_t>(b->nG + 1, s);
         int64_t total = partial_offsets(t, b, transpose, pofs, s);
         void* part = dev_alloc(rb * 3 * (size_t)(total > 0 ? total : 1), s);
@@ -435,6 +447,13 @@ hh_status hh_predict(hh_ctx* ctx, const double* X_dev, const double* F_dev, cons
         gather_rows(F_dev, t->perm, t->n, Fs, s);
         void* y = dev_alloc(rb * 3 * (size_t)t->n, s);
         near_field(ctx, t, b, *p, Fs, y, 0, s);
+        ctx->stats.t_short = 0.0;
+        ctx->stats.n_short_pairs = 0;
+        if ((p->flags & HH_FLAG_SHORT_RANGE) && p->shard_id == 0) {
+            HH_CUDA(cudaEventRecord(ev[6], s));
+            short_range_add(ctx, t->Xs, Fs, t->n, t->offsets, t->d_offsets, *p, y, rb == 8, s);
+            HH_CUDA(cudaEventRecord(ev[7], s));
+        }
         HH_CUDA(cudaEventRecord(ev[3], s));
         int64_t* pofs = dev_alloc_t<int64_t>(b->nG + 1, s);
         int64_t total = partial_offsets(t, b, 0, pofs, s);
@@ -461,6 +480,11 @@ hh_status hh_predict(hh_ctx* ctx, const double* X_dev, const double* F_dev, cons
         ctx->stats.t_tree = ms[0];
         ctx->stats.t_part = ms[1];
         ctx->stats.t_near = ms[2];
+        if ((p->flags & HH_FLAG_SHORT_RANGE) && p->shard_id == 0) {
+            float msr = 0.f;
+            HH_CUDA(cudaEventElapsedTime(&msr, ev[6], ev[7]));
+            ctx->stats.t_short = msr;
+        }
         ctx->stats.t_aca = ms[3];
         ctx->stats.t_apply = 0.0;
         ctx->stats.t_acc = ms[4];
@@ -529,6 +553,10 @@ hh_status hh_matvec_backward(hh_ctx* ctx, const hh_hmat* h, const double* gU_dev
                              double* gX_dev, float* gtheta_dev, void* stream)
 {
     if (!ctx || !h) return HH_ERR_ARG;
+    if (h->params.flags & HH_FLAG_SHORT_RANGE) {
+        ctx->err = "the adjoint covers M^(1) + M^(t,2) only: build the H-matrix without HH_FLAG_SHORT_RANGE";
+        return HH_ERR_ARG;
+    }
     if (gF_dev) {
         // dL/dF = alpha_1 gU + M_H^T gU: the transposed product
         hh_status st = hh_matvec(ctx, h, gU_dev, gF_dev, 1, stream);
@@ -619,6 +647,65 @@ hh_status hh_stats(hh_ctx* ctx, hh_stats_t* out)
     return guarded(ctx, [&]() {
         *out = ctx->stats;
         return HH_OK;
+    });
+}
+
+hh_status hh_set_short_range(hh_ctx* ctx, const float* theta_s_dev, const float* theta_3_dev, int width,
+                             double r_cut, void* stream)
+{
+    if (!ctx) return HH_ERR_ARG;
+    return guarded(ctx, [&]() {
+        HH_REQUIRE(width == 32 || width == 64, HH_ERR_ARG, "width must be 32 or 64");
+        HH_REQUIRE(r_cut > 0.0 && std::isfinite(r_cut), HH_ERR_ARG, "r_cut must be finite and > 0");
+        HH_REQUIRE(theta_s_dev || theta_3_dev, HH_ERR_ARG, "both networks are NULL");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int ns = 4 * width + width + 2 * (width * width + width) + 6 * width + 6;
+        const int n3 = 7 * width + width + 2 * (width * width + width) + 12 * width + 12;
+        HH_CUDA(cudaStreamSynchronize(s));
+        cudaFree(ctx->sr_theta_s32); cudaFree(ctx->sr_theta_332);
+        cudaFree(ctx->sr_theta_s64); cudaFree(ctx->sr_theta_364);
+        ctx->sr_theta_s32 = ctx->sr_theta_332 = nullptr;
+        ctx->sr_theta_s64 = ctx->sr_theta_364 = nullptr;
+        ctx->sr_width = 0;
+        HH_CUDA(cudaMalloc(&ctx->sr_theta_s32, sizeof(float) * ns));
+        HH_CUDA(cudaMalloc(&ctx->sr_theta_332, sizeof(float) * n3));
+        HH_CUDA(cudaMalloc(&ctx->sr_theta_s64, sizeof(double) * ns));
+        HH_CUDA(cudaMalloc(&ctx->sr_theta_364, sizeof(double) * n3));
+        if (theta_s_dev) HH_CUDA(cudaMemcpyAsync(ctx->sr_theta_s32, theta_s_dev, sizeof(float) * ns, cudaMemcpyDeviceToDevice, s));
+        else HH_CUDA(cudaMemsetAsync(ctx->sr_theta_s32, 0, sizeof(float) * ns, s));
+        if (theta_3_dev) HH_CUDA(cudaMemcpyAsync(ctx->sr_theta_332, theta_3_dev, sizeof(float) * n3, cudaMemcpyDeviceToDevice, s));
+        else HH_CUDA(cudaMemsetAsync(ctx->sr_theta_332, 0, sizeof(float) * n3, s));
+        k_widen<<<(ns + 255) / 256, 256, 0, s>>>(ctx->sr_theta_s32, ctx->sr_theta_s64, ns);
+        HH_CHECK_LAUNCH();
+        k_widen<<<(n3 + 255) / 256, 256, 0, s>>>(ctx->sr_theta_332, ctx->sr_theta_364, n3);
+        HH_CHECK_LAUNCH();
+        HH_CUDA(cudaStreamSynchronize(s));
+        ctx->sr_width = width;
+        ctx->sr_two_body = theta_s_dev != nullptr;
+        ctx->sr_three_body = theta_3_dev != nullptr;
+        ctx->sr_rcut = r_cut;
+        return HH_OK;
+    });
+}
+
+hh_status hh_short_range(hh_ctx* ctx, const double* X_dev, const double* F_dev, const int64_t* offsets,
+                         int32_t batch, const hh_params* p, void* stream, double* U_dev)
+{
+    if (!ctx) return HH_ERR_ARG;
+    return guarded(ctx, [&]() -> hh_status {
+        HH_REQUIRE(p != nullptr && X_dev && F_dev && U_dev && offsets, HH_ERR_ARG, "NULL argument");
+        HH_REQUIRE(batch >= 1 && offsets[0] == 0, HH_ERR_ARG, "bad offsets");
+        for (int32_t b = 0; b < batch; ++b) HH_REQUIRE(offsets[b + 1] >= offsets[b], HH_ERR_ARG, "bad offsets");
+        HH_REQUIRE(ctx->sr_width > 0, HH_ERR_ARG, "hh_set_short_range was not called");
+        HH_REQUIRE(p->radius > 0.0, HH_ERR_ARG, "radius must be > 0");
+        cudaStream_t s = (cudaStream_t)stream;
+        reset_call(ctx, s);
+        std::vector<int64_t> off(offsets, offsets + batch + 1);
+        int64_t* d_off = dev_alloc_t<int64_t>(batch + 1, s);
+        HH_CUDA(cudaMemcpyAsync(d_off, offsets, sizeof(int64_t) * (batch + 1), cudaMemcpyHostToDevice, s));
+        short_range_add(ctx, X_dev, F_dev, off[batch], off, d_off, *p, U_dev, 1, s);
+        dev_free(d_off, s);
+        return read_status(ctx, s);
     });
 }
 

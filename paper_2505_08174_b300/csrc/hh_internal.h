@@ -29,6 +29,14 @@ struct hh_ctx {
     int kev_near_used = 0;
     unsigned long long launch_base = 0;  // g_hh_launches at the start of the call
     hh_launch_cfg launch{};              // 0 fields: defaults (see resolved_launch)
+    // short-range networks (hh_set_short_range): FP32 and FP64 copies
+    float* sr_theta_s32 = nullptr;
+    float* sr_theta_332 = nullptr;
+    double* sr_theta_s64 = nullptr;
+    double* sr_theta_364 = nullptr;
+    int sr_width = 0;
+    int sr_two_body = 0, sr_three_body = 0;
+    double sr_rcut = 0.0;
 };
 
 // Launch shape with defaults filled in; tc selects the tensor-core defaults.
@@ -158,6 +166,12 @@ void near_field_tc(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_p
 void eval_pairs_tc(hh_ctx* ctx, const double* r, int64_t n, double a, double* K, cudaStream_t s);
 // SIMT K(r) for a list of separations (hh_near.cu), FP32 or FP64 per p.
 void eval_pairs_simt(hh_ctx* ctx, const hh_params& p, const double* r, int64_t n, double* K, cudaStream_t s);
+
+// Short-range terms of Eq. 6 (hh_short.cu): y[i] (FP64 if y_double, else
+// float; same order as X and F) += the two- and three-body sums over
+// neighbours within R_cut; offsets / d_offsets delimit the suspensions.
+void short_range_add(hh_ctx* ctx, const double* X, const double* F, int64_t n, const std::vector<int64_t>& offsets,
+                     const int64_t* d_offsets, const hh_params& p, void* y, int y_double, cudaStream_t s);
 
 // Adjoint: dL/dX (added to gX, caller order) and dL/dtheta (added to gtheta)
 // of L = sum w . (M_H F) with frozen pivots (hh_backward.cu); Fs, Ws sorted.
