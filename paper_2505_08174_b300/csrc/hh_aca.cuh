@@ -15,6 +15,7 @@ constexpr int SMALL_MAX = 32 * WARP_ROWS;
 template <typename R>
 struct AcaArgs {
     const double* Xs;
+    const float* Xp;  // FP32 (hi, lo) positions (tensor-core kernels)
     const R* th_g;   // parameters in global memory (copied to shared)
     int n_th;
     PairParams pp;
@@ -241,6 +242,7 @@ AcaArgs<R> make_aca_args(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, con
 {
     AcaArgs<R> A{};
     A.Xs = t->Xs;
+    A.Xp = t->Xp;
     A.th_g = theta_for<R>(ctx, p, &A.n_th);
     A.pp = PairParams{p.radius, p.viscosity};
     A.Fs = r.Fs;

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
         float f[4], id = 1.f;
         if (valid) {
             float rx, ry, rz;
-            sep<float>(A.Xs, pass == 0 ? t0 + x : t0 + bi, pass == 0 ? s0 + j : s0 + x, rx, ry, rz);
+            sep_split(A.Xp, pass == 0 ? t0 + x : t0 + bi, pass == 0 ? s0 + j : s0 + x, rx, ry, rz);
             features(rx, ry, rz, a, f, id);
         } else {
             f[0] = 1.f; f[1] = f[2] = 0.f; f[3] = a;

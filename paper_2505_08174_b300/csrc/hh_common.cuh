@@ -281,6 +281,21 @@ __device__ __forceinline__ void sep(const double* __restrict__ X, int64_t t, int
     rz = (R)(X[3 * t + 2] - X[3 * s + 2]);
 }
 
+// Positions as FP32 pairs, [n][6] = (x_hi, y_hi, z_hi, x_lo, y_lo, z_lo) with
+// v_hi = float(v), v_lo = float(v - v_hi): r = (hi_t - hi_s) + (lo_t - lo_s)
+// in FP32 is within ~1e-7 relative of the FP64 difference (the hi difference
+// of two nearby particles is exact, the lo parts carry the bits the hi parts
+// dropped), at FP32 cost.
+__device__ __forceinline__ void sep_split(const float* __restrict__ P, int64_t t, int64_t s, float& rx, float& ry,
+                                          float& rz)
+{
+    const float* a = P + 6 * t;
+    const float* b = P + 6 * s;
+    rx = (a[0] - b[0]) + (a[3] - b[3]);
+    ry = (a[1] - b[1]) + (a[4] - b[4]);
+    rz = (a[2] - b[2]) + (a[5] - b[5]);
+}
+
 // ---------------------------------------------------------------------------
 // Reductions
 // ---------------------------------------------------------------------------

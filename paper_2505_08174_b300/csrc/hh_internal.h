@@ -60,6 +60,7 @@ struct hh_tree {
     int32_t* perm = nullptr;         // [n] sorted position -> caller row
     uint64_t* codes = nullptr;       // [n] sorted Morton codes
     double* Xs = nullptr;            // [n,3] positions in sorted order
+    float* Xp = nullptr;             // [n,6] the same as FP32 (hi, lo) pairs (sep_split)
     int32_t n_nodes = 0;
     int32_t* nbeg = nullptr;         // [n_nodes]
     int32_t* nend = nullptr;

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(TC_T, 4) k_eval_pairs_tc(const double* __restr
 // the MLP, each row's contribution K F_n goes to shared memory and thread m
 // adds the rows of its target in increasing order (bit-reproducible).
 template <int W>
-__global__ void __launch_bounds__(TC_T, 4) k_near_tc(const double* __restrict__ Xs, const double* __restrict__ Fs,
+__global__ void __launch_bounds__(TC_T, 4) k_near_tc(const float* __restrict__ Xp, const double* __restrict__ Fs,
                                                     const int32_t* __restrict__ PH, const int64_t* __restrict__ rowH,
                                                     const int32_t* __restrict__ work, int64_t n_work,
                                                     const int32_t* __restrict__ nbeg, const int32_t* __restrict__ nend,
@@ -104,8 +104,8 @@ __global__ void __launch_bounds__(TC_T, 4) k_near_tc(const double* __restrict__ 
                 }
                 if (valid) {
                     float rx, ry, rz;
-                    if (!transpose) sep<float>(Xs, gm, gn, rx, ry, rz);
-                    else sep<float>(Xs, gn, gm, rx, ry, rz);
+                    if (!transpose) sep_split(Xp, gm, gn, rx, ry, rz);
+                    else sep_split(Xp, gn, gm, rx, ry, rz);
                     features(rx, ry, rz, a, f, id);
                 } else {
                     f[0] = 1.f; f[1] = f[2] = 0.f; f[3] = a;
@@ -165,13 +165,13 @@ void near_field_tc(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_p
     if (ctx->width == 32) {
         const size_t smem = near_smem_bytes<32>();
         HH_CUDA(cudaFuncSetAttribute(k_near_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_near_tc<32><<<(unsigned)grid, TC_T, smem, s>>>(t->Xs, Fs, b->PH, b->rowH, work, n_work, t->nbeg, t->nend,
+        k_near_tc<32><<<(unsigned)grid, TC_T, smem, s>>>(t->Xp, Fs, b->PH, b->rowH, work, n_work, t->nbeg, t->nend,
                                                          ctx->theta32, (float)p.radius, transpose, y,
                                                          ctx->d_counters + 5, ctx->d_status);
     } else {
         const size_t smem = near_smem_bytes<64>();
         HH_CUDA(cudaFuncSetAttribute(k_near_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_near_tc<64><<<(unsigned)grid, TC_T, smem, s>>>(t->Xs, Fs, b->PH, b->rowH, work, n_work, t->nbeg, t->nend,
+        k_near_tc<64><<<(unsigned)grid, TC_T, smem, s>>>(t->Xp, Fs, b->PH, b->rowH, work, n_work, t->nbeg, t->nend,
                                                          ctx->theta32, (float)p.radius, transpose, y,
                                                          ctx->d_counters + 5, ctx->d_status);
     }

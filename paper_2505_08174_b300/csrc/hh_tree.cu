@@ -215,6 +215,19 @@ __global__ void k_boxes(const double* __restrict__ Xs, const int32_t* __restrict
     }
 }
 
+// FP32 (hi, lo) copy of the sorted positions (see sep_split).
+__global__ void k_split_pos(const double* __restrict__ X, int64_t n, float* __restrict__ P)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int u = 0; u < 3; ++u) {
+        const double v = X[3 * i + u];
+        const float h = (float)v;
+        P[6 * i + u] = h;
+        P[6 * i + 3 + u] = (float)(v - (double)h);
+    }
+}
+
 }  // namespace
 
 void gather_rows(const double* in, const int32_t* perm, int64_t n, double* out, cudaStream_t s)
@@ -227,7 +240,7 @@ void gather_rows(const double* in, const int32_t* perm, int64_t n, double* out, 
 void free_tree(hh_tree* t)
 {
     if (!t) return;
-    cudaFree(t->d_offsets); cudaFree(t->perm); cudaFree(t->codes); cudaFree(t->Xs);
+    cudaFree(t->d_offsets); cudaFree(t->perm); cudaFree(t->codes); cudaFree(t->Xs); cudaFree(t->Xp);
     cudaFree(t->nbeg); cudaFree(t->nend); cudaFree(t->child); cudaFree(t->parent);
     cudaFree(t->lo); cudaFree(t->hi);
     delete t;
@@ -256,6 +269,7 @@ hh_tree* build_tree_impl(hh_ctx* ctx, const double* X, const int64_t* offsets, i
         HH_CUDA(cudaMalloc(&t->perm, sizeof(int32_t) * n));
         HH_CUDA(cudaMalloc(&t->codes, sizeof(uint64_t) * n));
         HH_CUDA(cudaMalloc(&t->Xs, sizeof(double) * 3 * n));
+        HH_CUDA(cudaMalloc(&t->Xp, sizeof(float) * 6 * n));
 
         // 1. Morton codes per instance
         double* bb = dev_alloc_t<double>(6 * batch, s);
@@ -279,6 +293,8 @@ hh_tree* build_tree_impl(hh_ctx* ctx, const double* X, const int64_t* offsets, i
         k_gather_codes<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(codes0, t->perm, n, t->codes);
         HH_CHECK_LAUNCH();
         gather_rows(X, t->perm, n, t->Xs, s);
+        k_split_pos<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(t->Xs, n, t->Xp);
+        HH_CHECK_LAUNCH();
         dev_free(codes0, s);
         dev_free(keys, s);
         dev_free(bb, s);
