@@ -72,6 +72,11 @@ enum { HH_MLP = 0, HH_RPY = 1 };                  /* hh_params.kernel    */
  * hh_matvec (forward only; the transposed product and the adjoint refuse
  * the flag with HH_ERR_ARG). */
 #define HH_FLAG_SHORT_RANGE 1
+/* hh_params.flags for hh_aca: keep ranks and pivots only, no factors (memory
+ * O(blocks x max_rank) instead of O(sum (c+q) rank)).  Such an H-matrix
+ * serves hh_matvec_backward, which rebuilds each block's factors in FP64
+ * along the stored pivots; hh_matvec refuses it (HH_ERR_ARG). */
+#define HH_FLAG_PIVOTS_ONLY 2
 
 typedef struct {
     int32_t leaf_size;   /* C_leaf: a cluster is a leaf iff |tau| < C_leaf (Def. 1); 2..129 */
@@ -192,15 +197,20 @@ hh_status hh_aca_block_apply_noalloc(hh_ctx *ctx, const double *Xt_dev, int32_t 
                                      const double *F_dev, const hh_params *p, void *stream, double *y_dev,
                                      int32_t *rank_dev);
 
-/* Adjoint of L = sum_i gU_i . U_i for U = alpha_1 F + M_H F built by hh_aca
+/* (With an H-matrix built under HH_FLAG_PIVOTS_ONLY, gF_dev too comes from
+ * the FP64 factors rebuilt along the pivots, its admissible-block part summed
+ * with FP64 atomics: equal to the transposed product up to summation order.)
+ *
+ * Adjoint of L = sum_i gU_i . U_i for U = alpha_1 F + M_H F built by hh_aca
  * with the MLP kernel (Section 3, Eqs. 4 and 8 differentiated; the paper
  * trains the MLP on pairs and has no H-matrix adjoint): gF_dev = alpha_1 gU
  * + M_H^T gU (FP64 [N,3]), gX_dev += dL/dX (FP64 [N,3]) and gtheta_dev +=
  * dL/dtheta (float32, length of theta), the last two with tree, partition
  * and ACA pivots frozen, evaluated in FP64.  For an FP32 or BF16 h, dL/dX and
  * dL/dtheta are those of the FP64 H-matrix on the same tree and partition
- * (its ACA is run inside the call): pivots picked from low-precision
- * residuals do not give a usable derivative of the rank recursion.  Any of
+ * (its ACA, pivots only, is run inside the call): pivots picked from
+ * low-precision residuals do not give a usable derivative of the rank
+ * recursion.  Any of
  * gF_dev, gX_dev, gtheta_dev may be NULL; gX and gtheta are accumulated
  * into (zero them first).  Near-field activations are recomputed, not
  * stored. */

@@ -121,10 +121,12 @@ def lib():
 
 
 FLAG_SHORT_RANGE = 1
+FLAG_PIVOTS_ONLY = 2
 
 
 def Params(leaf_size=32, eta=1.0, eps=1e-4, max_rank=48, precision="fp32", kernel="mlp", radius=1.0,
-           viscosity=1.0, j1_rule=0, seed=0, shard_id=0, n_shards=1, short_range=False) -> CParams:
+           viscosity=1.0, j1_rule=0, seed=0, shard_id=0, n_shards=1, short_range=False,
+           pivots_only=False) -> CParams:
     p = CParams()
     lib().hh_default_params(ctypes.byref(p))
     p.leaf_size, p.eta, p.eps, p.max_rank = leaf_size, eta, eps, max_rank
@@ -132,7 +134,7 @@ def Params(leaf_size=32, eta=1.0, eps=1e-4, max_rank=48, precision="fp32", kerne
     p.kernel = KERNELS[kernel] if isinstance(kernel, str) else kernel
     p.radius, p.viscosity, p.j1_rule, p.seed = radius, viscosity, j1_rule, seed
     p.shard_id, p.n_shards = shard_id, n_shards
-    p.flags = FLAG_SHORT_RANGE if short_range else 0
+    p.flags = (FLAG_SHORT_RANGE if short_range else 0) | (FLAG_PIVOTS_ONLY if pivots_only else 0)
     return p
 
 

@@ -63,9 +63,19 @@ void check_params(const hh_ctx* ctx, const hh_params* p)
     HH_REQUIRE(p->radius > 0.0 && p->viscosity > 0.0, HH_ERR_ARG, "radius and viscosity must be > 0");
     HH_REQUIRE(p->n_shards >= 1 && p->shard_id >= 0 && p->shard_id < p->n_shards, HH_ERR_ARG, "bad shard");
     HH_REQUIRE(p->j1_rule == 0 || p->j1_rule == 1, HH_ERR_ARG, "j1_rule must be 0 or 1");
-    HH_REQUIRE((p->flags & ~HH_FLAG_SHORT_RANGE) == 0, HH_ERR_ARG, "unknown flags");
+    HH_REQUIRE((p->flags & ~(HH_FLAG_SHORT_RANGE | HH_FLAG_PIVOTS_ONLY)) == 0, HH_ERR_ARG, "unknown flags");
     HH_REQUIRE(!(p->flags & HH_FLAG_SHORT_RANGE) || ctx->sr_width > 0, HH_ERR_ARG,
                "HH_FLAG_SHORT_RANGE needs hh_set_short_range");
+}
+
+// gF[perm[m]] = a1 w(m) + near^T w (m) + far^T w (m), sorted inputs.
+__global__ void k_gf_out(const double* __restrict__ Ws, const double* __restrict__ y, const double* __restrict__ far,
+                         const int32_t* __restrict__ perm, int64_t n, double a1, double* __restrict__ gF)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const int64_t i = perm[m];
+    for (int u = 0; u < 3; ++u) gF[3 * i + u] = a1 * Ws[3 * m + u] + y[3 * m + u] + far[3 * m + u];
 }
 
 __global__ void k_fill(double* __restrict__ a, int64_t n, double v)
@@ -346,11 +356,13 @@ hh_status hh_aca(hh_ctx* ctx, const hh_tree* tree, const hh_blocks* blocks, cons
             HH_CUDA(cudaStreamSynchronize(s));
             dev_free(len, s);
         }
-        HH_CUDA(cudaMalloc(&h->factors, (size_t)h->real_bytes * 9 * (h->n_factor > 0 ? h->n_factor : 1)));
-        r.factors = h->factors;
-        r.fofs = h->fofs;
-        r.mode = 2;
-        aca_run(ctx, tree, blocks, *p, r, s);
+        if (!(p->flags & HH_FLAG_PIVOTS_ONLY)) {
+            HH_CUDA(cudaMalloc(&h->factors, (size_t)h->real_bytes * 9 * (h->n_factor > 0 ? h->n_factor : 1)));
+            r.factors = h->factors;
+            r.fofs = h->fofs;
+            r.mode = 2;
+            aca_run(ctx, tree, blocks, *p, r, s);
+        }
         HH_CUDA(cudaEventRecord(ctx->ev[1], s));
         hh_status w = read_status(ctx, s);
         float ms = 0.f;
@@ -387,6 +399,7 @@ hh_status hh_matvec(hh_ctx* ctx, const hh_hmat* h, const double* F_dev, double* 
     if (!ctx || !h) return HH_ERR_ARG;
     return guarded(ctx, [&]() {
         HH_REQUIRE(F_dev && U_dev, HH_ERR_ARG, "F or U is NULL");
+        HH_REQUIRE(h->factors != nullptr, HH_ERR_ARG, "H-matrix built with HH_FLAG_PIVOTS_ONLY has no factors");
         cudaStream_t s = (cudaStream_t)stream;
         const hh_tree* t = h->tree;
         const hh_blocks* b = h->blocks;
@@ -557,20 +570,24 @@ hh_status hh_matvec_backward(hh_ctx* ctx, const hh_hmat* h, const double* gU_dev
         ctx->err = "the adjoint covers M^(1) + M^(t,2) only: build the H-matrix without HH_FLAG_SHORT_RANGE";
         return HH_ERR_ARG;
     }
-    if (gF_dev) {
+    const bool factors = h->factors != nullptr;
+    if (gF_dev && factors) {
         // dL/dF = alpha_1 gU + M_H^T gU: the transposed product
         hh_status st = hh_matvec(ctx, h, gU_dev, gF_dev, 1, stream);
         if (st != HH_OK) return st;
     }
-    if (!gX_dev && !gtheta_dev) return HH_OK;
+    const bool gF_here = gF_dev && !factors;
+    if (!gX_dev && !gtheta_dev && !gF_here) return HH_OK;
     // dL/dX and dL/dtheta differentiate the FP64 rank recursion: a narrower
-    // H-matrix is re-approximated in FP64 on the same tree and partition
+    // H-matrix is re-approximated in FP64 (pivots only) on the same tree and
+    // partition
     hh_hmat* h64 = nullptr;
     if (h->real_bytes != 8) {
         hh_params p64 = h->params;
         p64.precision = HH_FP64;
+        p64.flags |= HH_FLAG_PIVOTS_ONLY;
         hh_status st = hh_aca(ctx, h->tree, h->blocks, &p64, stream, &h64);
-        if (st != HH_OK) return st;
+        if (st != HH_OK && st != HH_WARN_RANK_CAP) return st;
     }
     const hh_hmat* hx = h64 ? h64 : h;
     hh_status st = guarded(ctx, [&]() -> hh_status {
@@ -581,7 +598,23 @@ hh_status hh_matvec_backward(hh_ctx* ctx, const hh_hmat* h, const double* gU_dev
         double* Ws = dev_alloc_t<double>(3 * t->n, s);
         gather_rows(F_dev, t->perm, t->n, Fs, s);
         gather_rows(gU_dev, t->perm, t->n, Ws, s);
-        matvec_backward_xtheta(ctx, hx, Fs, Ws, gX_dev, gtheta_dev, s);
+        double* gFs = nullptr;
+        if (gF_here) {
+            gFs = dev_alloc_t<double>(3 * t->n, s);
+            HH_CUDA(cudaMemsetAsync(gFs, 0, sizeof(double) * 3 * t->n, s));
+        }
+        matvec_backward_xtheta(ctx, hx, Fs, Ws, gX_dev, gtheta_dev, gFs, s);
+        if (gF_here) {
+            // near part (transposed, FP64) and alpha_1 w, then caller order
+            const hh_params& px = hx->params;
+            double* y = dev_alloc_t<double>(3 * t->n, s);
+            near_field(ctx, t, hx->blocks, px, Ws, y, 1, s);
+            const double a1 = px.shard_id == 0 ? alpha1(px) : 0.0;
+            k_gf_out<<<(unsigned)ceil_div(t->n, 256), 256, 0, s>>>(Ws, y, gFs, t->perm, t->n, a1, gF_dev);
+            HH_CHECK_LAUNCH();
+            dev_free(y, s);
+            dev_free(gFs, s);
+        }
         dev_free(Fs, s);
         dev_free(Ws, s);
         return HH_OK;

@@ -338,6 +338,64 @@ __device__ __forceinline__ void st9g(R* base, int64_t ld, int64_t x, const R* v)
     for (int e = 0; e < 9; ++e) base[e * ld + x] = v[e];
 }
 
+// Factors of one admissible block rebuilt along its frozen pivots (the
+// H-matrix was built with HH_FLAG_PIVOTS_ONLY): the recursion of Algorithm 2
+// without the pivot search.  C [l][9][c], then Q [l][9][q].
+template <typename R, int W>
+__device__ void refactor(const R* th, R a, const double* __restrict__ Xs, int32_t t0, int32_t c, int32_t s0,
+                         int32_t q, const int32_t* I, const int32_t* J, int l, R* C, R* Pi)
+{
+    const int lane = threadIdx.x & 31;
+    R* Q = C + (int64_t)l * 9 * c;
+    for (int k = 0; k < l; ++k) {
+        const int ik = I[k], jk = J[k];
+        R* Ck = C + (int64_t)k * 9 * c;
+        R* Qk = Q + (int64_t)k * 9 * q;
+        for (int m = lane; m < c; m += 32) {
+            R rx, ry, rz, K[9];
+            sep<R>(Xs, t0 + m, s0 + jk, rx, ry, rz);
+            entry_forward<R, W>(th, a, rx, ry, rz, K);
+            for (int p = 0; p < k; ++p) {
+                R cp[9], qp[9], t9[9];
+                ld9g(C + (int64_t)p * 9 * c, c, m, cp);
+                ld9g(Q + (int64_t)p * 9 * q, q, jk, qp);
+                mm3(cp, qp, t9);
+                for (int e = 0; e < 9; ++e) K[e] -= t9[e];
+            }
+            st9g(Ck, c, m, K);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            double P[9], Pd[9];
+            for (int e = 0; e < 9; ++e) P[e] = (double)Ck[(int64_t)e * c + ik];
+            inv3d(P, Pd);
+            for (int e = 0; e < 9; ++e) Pi[e] = (R)Pd[e];
+        }
+        __syncwarp();
+        for (int m = lane; m < c; m += 32) {
+            R v[9], o[9];
+            ld9g(Ck, c, m, v);
+            mm3(v, Pi, o);
+            st9g(Ck, c, m, o);
+        }
+        __syncwarp();
+        for (int n = lane; n < q; n += 32) {
+            R rx, ry, rz, K[9];
+            sep<R>(Xs, t0 + ik, s0 + n, rx, ry, rz);
+            entry_forward<R, W>(th, a, rx, ry, rz, K);
+            for (int p = 0; p < k; ++p) {
+                R cp[9], qp[9], t9[9];
+                ld9g(C + (int64_t)p * 9 * c, c, ik, cp);
+                ld9g(Q + (int64_t)p * 9 * q, q, n, qp);
+                mm3(cp, qp, t9);
+                for (int e = 0; e < 9; ++e) K[e] -= t9[e];
+            }
+            st9g(Qk, q, n, K);
+        }
+        __syncwarp();
+    }
+}
+
 template <typename R, int W>
 __global__ void __launch_bounds__(32) k_far_bwd(const double* __restrict__ Xs, const double* __restrict__ Fs,
                                                 const double* __restrict__ Ws, const int32_t* __restrict__ PG,
@@ -347,7 +405,8 @@ __global__ void __launch_bounds__(32) k_far_bwd(const double* __restrict__ Xs, c
                                                 int max_rank, int shard, int n_shards, const R* __restrict__ fac,
                                                 const int64_t* __restrict__ fofs, const R* __restrict__ th_g, R a,
                                                 R* __restrict__ scratch, int64_t ws_stride,
-                                                const int32_t* __restrict__ perm, double* gX, double* gth, R* gacc)
+                                                const int32_t* __restrict__ perm, double* gX, double* gth, R* gacc,
+                                                double* gFs)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BwdSmem<R, W>& sm = *reinterpret_cast<BwdSmem<R, W>*>(smem_raw);
@@ -355,6 +414,7 @@ __global__ void __launch_bounds__(32) k_far_bwd(const double* __restrict__ Xs, c
     bwd_setup<R, W>(sm, th_g, gacc);
     const int lane = threadIdx.x & 31;
     R* Cb = scratch + (int64_t)blockIdx.x * ws_stride;
+    R* Cw = Cb + ws_stride / 2;   // rebuilt factors when the H-matrix holds pivots only
     for (int64_t b = blockIdx.x; b < nG; b += gridDim.x) {
         if (b % n_shards != shard) continue;
         const int l = rank[b];
@@ -363,7 +423,8 @@ __global__ void __launch_bounds__(32) k_far_bwd(const double* __restrict__ Xs, c
         const int32_t t0 = nbeg[t], c = nend[t] - t0, s0 = nbeg[s], q = nend[s] - s0;
         const int32_t* I = pivI + b * max_rank;
         const int32_t* J = pivJ + b * max_rank;
-        const R* C = fac + 9 * fofs[b];
+        if (!fac) refactor<R, W>(sm.th, a, Xs, t0, c, s0, q, I, J, l, Cw, piT);
+        const R* C = fac ? fac + 9 * fofs[b] : Cw;
         const R* Q = C + (int64_t)l * 9 * c;
         R* Qb = Cb + (int64_t)l * 9 * c;
         auto Ck = [&](int k) { return C + (int64_t)k * 9 * c; };
@@ -391,6 +452,20 @@ __global__ void __launch_bounds__(32) k_far_bwd(const double* __restrict__ Xs, c
             }
         }
         __syncwarp();
+        if (gFs) {
+            // far part of dL/dF: (C Q)^T w restricted to this block's sources
+            for (int n = lane; n < q; n += 32) {
+                R g[3] = {0, 0, 0};
+                for (int k = 0; k < l; ++k) {
+                    R v[9];
+                    ld9g(Qk(k), q, n, v);
+                    const R* sk = sv + 3 * k;
+                    for (int u = 0; u < 3; ++u) g[u] += v[u] * sk[0] + v[3 + u] * sk[1] + v[6 + u] * sk[2];
+                }
+                double* out = gFs + 3 * (int64_t)(s0 + n);
+                for (int u = 0; u < 3; ++u) atomicAdd(&out[u], (double)g[u]);
+            }
+        }
         for (int k = 0; k < l; ++k) {
             for (int m = lane; m < c; m += 32) {
                 const double* w = Ws + 3 * (int64_t)(t0 + m);
@@ -544,7 +619,7 @@ __global__ void k_leafs(const int32_t* __restrict__ child, int32_t n, int shard,
 
 template <typename R, int W>
 void launch_bwd(hh_ctx* ctx, const hh_hmat* h, const double* Fs, const double* Ws, double* gX, double* gth,
-                cudaStream_t s)
+                double* gFs, cudaStream_t s)
 {
     const hh_tree* t = h->tree;
     const hh_blocks* b = h->blocks;
@@ -582,7 +657,8 @@ void launch_bwd(hh_ctx* ctx, const hh_hmat* h, const double* Fs, const double* W
         HH_CUDA(cudaMemcpyAsync(&max_cq, dmax, sizeof(int), cudaMemcpyDeviceToHost, s));
         HH_CUDA(cudaStreamSynchronize(s));
         dev_free(dmax, s);
-        const int64_t stride = (int64_t)max_cq * 9 * p.max_rank;   // Cb and Qb of one block
+        // Cb and Qb of one block, and the rebuilt factors when h holds pivots only
+        const int64_t stride = (int64_t)max_cq * 9 * p.max_rank * (h->factors ? 1 : 2);
         const int64_t budget = (int64_t)16 << 30;
         int64_t grid = std::min<int64_t>(b->nG, max_grid);
         grid = std::max<int64_t>(1, std::min<int64_t>(grid, budget / (stride * (int64_t)sizeof(R))));
@@ -590,7 +666,7 @@ void launch_bwd(hh_ctx* ctx, const hh_hmat* h, const double* Fs, const double* W
         k_far_bwd<R, W><<<(unsigned)grid, 32, smem, s>>>(t->Xs, Fs, Ws, b->PG, b->nG, t->nbeg, t->nend, h->rank,
                                                         h->pivI, h->pivJ, p.max_rank, p.shard_id, p.n_shards,
                                                         (const R*)h->factors, h->fofs, th, (R)p.radius, scratch,
-                                                        stride, t->perm, gX, gth, gacc);
+                                                        stride, t->perm, gX, gth, gacc, gFs);
         HH_CHECK_LAUNCH();
         dev_free(scratch, s);
     }
@@ -604,7 +680,7 @@ void launch_bwd(hh_ctx* ctx, const hh_hmat* h, const double* Fs, const double* W
 // dL/dX (accumulated into gX, caller order) and dL/dtheta (accumulated into
 // gtheta, float32) for L = sum w . (M_H F); Fs and Ws in sorted order.
 void matvec_backward_xtheta(hh_ctx* ctx, const hh_hmat* h, const double* Fs, const double* Ws, double* gX,
-                            float* gtheta, cudaStream_t s)
+                            float* gtheta, double* gFs, cudaStream_t s)
 {
     const hh_params& p = h->params;
     HH_REQUIRE(p.kernel == HH_MLP, HH_ERR_ARG, "dL/dX and dL/dtheta need the MLP kernel");
@@ -619,8 +695,8 @@ void matvec_backward_xtheta(hh_ctx* ctx, const hh_hmat* h, const double* Fs, con
     // narrower H-matrix in FP64): the cotangents of the rank loop cancel only
     // to the working rounding times the squared condition number of the 3x3
     // pivot blocks.
-    if (ctx->width == 32) launch_bwd<double, 32>(ctx, h, Fs, Ws, gX, gth, s);
-    else launch_bwd<double, 64>(ctx, h, Fs, Ws, gX, gth, s);
+    if (ctx->width == 32) launch_bwd<double, 32>(ctx, h, Fs, Ws, gX, gth, gFs, s);
+    else launch_bwd<double, 64>(ctx, h, Fs, Ws, gX, gth, gFs, s);
     if (gtheta) {
         k_theta_out<<<(unsigned)ceil_div(ctx->n_theta, 256), 256, 0, s>>>(gth, gtheta, ctx->n_theta);
         HH_CHECK_LAUNCH();

@@ -176,8 +176,10 @@ void short_range_add(hh_ctx* ctx, const double* X, const double* F, int64_t n, c
 
 // Adjoint: dL/dX (added to gX, caller order) and dL/dtheta (added to gtheta)
 // of L = sum w . (M_H F) with frozen pivots (hh_backward.cu); Fs, Ws sorted.
+// gFs (sorted order, may be NULL) += the admissible blocks' part of M_H^T w
+// (FP64 atomics), from the same pass.
 void matvec_backward_xtheta(hh_ctx* ctx, const hh_hmat* h, const double* Fs, const double* Ws, double* gX,
-                            float* gtheta, cudaStream_t s);
+                            float* gtheta, double* gFs, cudaStream_t s);
 
 // Training of the pair MLP (hh_train.cu).
 double train_loss_grad(hh_ctx* ctx, const float* theta, int width, const double* r, const double* e, const double* U,

@@ -190,3 +190,24 @@ def test_autograd_function_matches_direct_calls(ctx):
     assert np.abs(th.grad.cpu().numpy().astype(np.float64) - gT).max() <= 1e-6 * np.abs(gT).max()
     Ud, _ = loss(ctx, X0, F0, W, p)
     assert float(L.detach()) == pytest.approx(Ud, rel=1e-14)
+
+
+def test_pivots_only_hmatrix_gives_the_same_gradients(ctx):
+    n = 1500
+    X = hh_synth.rsa_cube(n, 0.1, seed=48)
+    F, W = hh_synth.forces(n, 15), hh_synth.forces(n, 16)
+    p = hh.Params(precision="fp64")
+    gF, gX, gT, _ = grads(ctx, X, F, W, p)
+    pp = hh.Params(precision="fp64", pivots_only=True)
+    t = ctx.build_tree(cuda(X), pp)
+    h = ctx.aca(t, ctx.partition(t, pp), pp)
+    with pytest.raises(hh.HHError):
+        ctx.matvec(h, cuda(F))
+    gF2 = torch.zeros((n, 3), dtype=torch.float64, device="cuda")
+    gX2 = torch.zeros_like(gF2)
+    gT2 = torch.zeros(len(THETA), dtype=torch.float32, device="cuda")
+    ctx.matvec_backward(h, cuda(W), cuda(F), gF=gF2, gX=gX2, gtheta=gT2)
+    # factors rebuilt along the same pivots: equal up to summation order
+    assert np.abs(gF2.cpu().numpy() - gF).max() <= 1e-12 * np.abs(gF).max()
+    assert np.abs(gX2.cpu().numpy() - gX).max() <= 1e-10 * np.abs(gX).max()
+    assert np.abs(gT2.cpu().numpy() - gT).max() <= 1e-5 * np.abs(gT).max()
