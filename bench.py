@@ -381,7 +381,7 @@ def run_workload(args):
                      "rel_err": float(oracle.rel_error(Ud, Uh[rows] - a1 * F[rows])), "gpu_launches": launches,
                      "clocks": clocks})
     elif args.workload == "grad200k":
-        n = 200000
+        n = args.n if args.n != 1_000_000 else 200000
         X = hh_synth.gaussian_cloud(n, 30.0, seed=7)[0]
         F, W = hh_synth.forces(n, 1), hh_synth.forces(n, 2)
         # forward U by the fused prediction; the adjoint rebuilds the FP64 factors along the pivots of a
@@ -404,7 +404,7 @@ def run_workload(args):
         line.update({"metric": "particle-gradients/sec: forward U and dL/dF, dL/dX, dL/dtheta of L = sum w.U",
                      "value": n * args.steps / (total_ms / 1e3), "unit": "particles/s",
                      "ms_per_step": total_ms / args.steps, "dtype": "f64",
-                     "config": {"workload": "gaussian_drop_N200000_sigma30a", "n": n, "leaf_size": args.leaf,
+                     "config": {"workload": f"gaussian_drop_N{n}_sigma30a", "n": n, "leaf_size": args.leaf,
                                 "eps": args.eps, "l2": "flushed between steps (256 MB write)"},
                      "gpu_launches": launches, "clocks": clocks})
     elif args.workload == "cube10m":

@@ -361,8 +361,8 @@ __global__ void k_max_dim(const int32_t* __restrict__ work, int64_t n, const int
 // Size classes of the sorted large list (keys: (2^31 - 1 - (c + q)) << 32 | b,
 // ascending = decreasing c + q): pos[i] = first item with c + q <= lim[i],
 // mx[i] = c + q of item pos[i - 1] (class i's largest), mx[0] = the first item's.
-constexpr int N_CLASS_LIMITS = 3;
-__constant__ int32_t c_class_lim[N_CLASS_LIMITS] = {16384, 4096, 1536};
+constexpr int N_CLASS_LIMITS = 5;
+__constant__ int32_t c_class_lim[N_CLASS_LIMITS] = {262144, 65536, 16384, 4096, 1536};
 
 __global__ void k_class_bounds(const uint64_t* __restrict__ key, int64_t n, int64_t* __restrict__ pos,
                                int32_t* __restrict__ mx)
@@ -396,7 +396,7 @@ void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_
             // factors (max_rank x 9 x (c+q) reals) + c+q flag bytes, rounded to 256 B
             int64_t stride = (int64_t)k.max_cq * 9 * mr + ceil_div(k.max_cq, (int64_t)sizeof(R));
             stride = ceil_div(stride * (int64_t)sizeof(R), 256) * 256 / (int64_t)sizeof(R);
-            const int64_t budget = (int64_t)24 << 30;  // bytes of large-team workspace
+            const int64_t budget = aca_workspace_budget();  // bytes of large-team workspace
             int64_t teams = std::min<int64_t>(k.end - k.begin, (int64_t)lc.aca_large_cps * ctx->n_sm);
             teams = std::max<int64_t>(1, std::min<int64_t>(teams, budget / (stride * (int64_t)sizeof(R))));
             R* scratch = dev_alloc_t<R>(stride * teams, s);

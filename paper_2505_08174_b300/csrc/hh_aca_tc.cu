@@ -390,7 +390,7 @@ void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_par
             const AcaClass& k = cls[i];
             int64_t stride = (int64_t)k.max_cq * 9 * mr + ceil_div(k.max_cq, (int64_t)sizeof(float));
             stride = ceil_div(stride * (int64_t)sizeof(float), 256) * 256 / (int64_t)sizeof(float);
-            const int64_t budget = (int64_t)24 << 30;
+            const int64_t budget = aca_workspace_budget();
             int64_t teams = std::min<int64_t>(k.end - k.begin, (int64_t)lc.aca_large_cps * ctx->n_sm);
             teams = std::max<int64_t>(1, std::min<int64_t>(teams, budget / (stride * (int64_t)sizeof(float))));
             float* scratch = dev_alloc_t<float>(stride * teams, s);

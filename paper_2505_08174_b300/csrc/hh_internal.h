@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -153,6 +154,15 @@ struct AcaClass {
     int64_t begin, end;
     int32_t max_cq;
 };
+
+// Bytes the CTA-team ACA launches may take for their factor workspaces: half
+// of the device memory free at the time, at least 4 GB (grids shrink to fit).
+inline int64_t aca_workspace_budget()
+{
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return (int64_t)24 << 30;
+    return std::max<int64_t>((int64_t)4 << 30, (int64_t)(fr / 2));
+}
 
 // Tensor-core ACA (hh_aca_tc.cu, precision HH_BF16 with the MLP kernel) over
 // the small (warp-team) and large (CTA-team) work lists built by aca_run.
