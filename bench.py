@@ -125,6 +125,21 @@ def aca_traffic(queries):
     return None if ACA_TC_DRAM_BYTES_PER_QUERY is None else ACA_TC_DRAM_BYTES_PER_QUERY * queries
 
 
+def weak_scaling_value(n_local, steps, total_ms_local, dist=None, device="cpu"):
+    """Whole-job particle-velocities/s: the particles of every rank's own
+    suspension over the slowest rank's time (max over ranks); returns
+    (value, max total ms).  Without a process group, the local figures."""
+    n_total, t_ms = float(n_local), float(total_ms_local)
+    if dist is not None and dist.is_available() and dist.is_initialized():
+        import torch
+        x = torch.tensor([t_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        m = torch.tensor([n_total], dtype=torch.float64, device=device)
+        dist.all_reduce(m, op=dist.ReduceOp.SUM)
+        t_ms, n_total = float(x.item()), float(m.item())
+    return n_total * steps / (t_ms / 1e3), t_ms
+
+
 def workload(n, seed_geom=1234):
     import hh_synth
     X = hh_synth.rsa_cube(n, 0.1, seed=seed_geom)
@@ -213,12 +228,7 @@ def run_ours(args, rank, world):
     if dist:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(np.sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = n * world * args.steps / (total_ms / 1e3)
+    value, total_ms = weak_scaling_value(n, args.steps, float(np.sum(step_ms)), dist, "cuda")
     clocks = clk.summary()
     st = ctx.stats()
 
