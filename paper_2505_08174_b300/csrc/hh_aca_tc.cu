@@ -212,6 +212,23 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
         } else {
             f[0] = 1.f; f[1] = f[2] = 0.f; f[3] = a;
         }
+        // the residual update below reads element e of C_p (Q_p) for the team's
+        // rows x0 .. x0 + SIZE - 1 and every p < k: request those lines into
+        // L2 now, so the loads find them there after the MLP chain
+        if (b >= 0 && k > 0) {
+            const int lane = threadIdx.x & 31;
+            const float* fac0 = pass == 0 ? Cs : Qs;
+            const int x1 = min(x0 + SIZE, nx) - 1;
+            const int wbase = x0 + (tid & ~31);            // this warp's first row
+            if (wbase <= x1) {
+                const int wlast = min(wbase + 31, x1);
+                for (int idx = lane; idx < 18 * k; idx += 32) {
+                    const int pe = idx >> 1;
+                    const float* a = fac0 + (int64_t)pe * nx + ((idx & 1) ? wlast : wbase);
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+                }
+            }
+        }
         float o[6];
         if (exhausted) break;   // uniform over the team
         // warps without a valid row skip the chain; a warp whose chain timed
