@@ -118,7 +118,7 @@ class ClockSampler:
 # one ncu capture of every k_aca_tc launch of a prediction at N = 100,000
 # (profiles/k_aca_tc_bf16_n100k.md); the traffic of a launch is taken as
 # proportional to its queries.
-ACA_TC_DRAM_BYTES_PER_QUERY = 400.0
+ACA_TC_DRAM_BYTES_PER_QUERY = 418.0
 
 
 def aca_traffic(queries):
