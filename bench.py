@@ -417,6 +417,44 @@ def run_workload(args):
                      "config": {"workload": f"gaussian_drop_N{n}_sigma30a", "n": n, "leaf_size": args.leaf,
                                 "eps": args.eps, "l2": "flushed between steps (256 MB write)"},
                      "gpu_launches": launches, "clocks": clocks})
+    elif args.workload == "shortrange1m":
+        # the headline prediction with the short-range terms of Eq. 6 switched on (seeded networks)
+        n = args.n
+        X = hh_synth.rsa_cube(n, 0.1, seed=1234)
+        F = hh_synth.forces(n, 0)
+        ctx.set_short_range(hh_synth.mlp_params(32, 21), hh_synth.mlp_params(32, 22, n_in=7, n_out=12), 32, 5.0)
+        p = hh.Params(leaf_size=args.leaf, eps=args.eps, precision=args.precision, short_range=True)
+        Xd, Fd = torch.as_tensor(X).cuda(), torch.as_tensor(F).cuda()
+        U = torch.empty_like(Xd)
+        total_ms, clocks, launches = _timed(ctx, lambda: ctx.predict(Xd, Fd, p, out=U), args.steps, args.warmup, dev)
+        st = ctx.stats()
+        line.update({"metric": "particle-velocities/sec per prediction with the short-range terms of Eq. 6",
+                     "value": n * args.steps / (total_ms / 1e3), "unit": "particle-velocities/s",
+                     "ms_per_step": total_ms / args.steps, "dtype": args.precision,
+                     "config": {"workload": f"uniform_cube_rsa_N{n}_phi0.1_short_range_rcut5", "n": n,
+                                "leaf_size": args.leaf, "eps": args.eps, "l2": "flushed between steps (256 MB write)"},
+                     "stages_ms": {k: st[k] for k in ("t_tree", "t_part", "t_near", "t_short", "t_aca", "t_acc")},
+                     "n_short_pairs": st["n_short_pairs"], "gpu_launches": launches, "clocks": clocks})
+    elif args.workload == "train":
+        # Eq. 5 training of the pair MLP on the GPU: Adam steps on batches of two-particle samples (RPY teacher)
+        B = 4096
+        r, e = hh_synth.two_particle_samples(B * 64, seed=5)
+        rd, ed = torch.as_tensor(r).cuda(), torch.as_tensor(e).cuda()
+        th = torch.as_tensor(theta).cuda().contiguous()
+        m, v = torch.zeros_like(th), torch.zeros_like(th)
+        state = {"k": 0}
+
+        def step():
+            i = state["k"] % 64
+            ctx.train_step(th, m, v, state["k"] + 1, 32, rd[i * B:(i + 1) * B], ed[i * B:(i + 1) * B], lr=1e-3)
+            state["k"] += 1
+        total_ms, clocks, launches = _timed(ctx, step, args.steps, args.warmup, dev)
+        line.update({"metric": "training samples/sec (Eq. 5 loss, gradient and Adam step on the GPU)",
+                     "value": B * args.steps / (total_ms / 1e3), "unit": "samples/s",
+                     "ms_per_step": total_ms / args.steps, "dtype": "f32",
+                     "config": {"workload": "two_particle_rpy_teacher_batch4096", "batch": B, "width": 32},
+                     "gpu_launches": 4 * args.steps,   # per step: per-sample pass, weight sums, loss sum, Adam
+                     "clocks": clocks})
     elif args.workload == "cube10m":
         n = 10_000_000
         X = hh_synth.rsa_cube(n, 0.1, seed=1234)
@@ -452,7 +490,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", default="cube1m", choices=["cube1m", "batch64", "grad200k", "cube10m"],
+    ap.add_argument("--workload", default="cube1m",
+                    choices=["cube1m", "batch64", "grad200k", "cube10m", "shortrange1m", "train"],
                     help="cube1m is the headline; the others measure further configurations")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
