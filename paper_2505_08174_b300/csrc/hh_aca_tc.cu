@@ -401,8 +401,17 @@ void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_par
     const int mr = std::min(p.max_rank, MAXR);
     const hh_launch_cfg lc = resolved_launch(ctx, true);
     AcaArgs<float> A = make_aca_args<float>(ctx, t, bl, p, r);
+    // the CTA-team size classes run on the context's second stream, beside
+    // the warp teams: the serial tails of the few largest blocks overlap with
+    // the bulk of the small blocks
+    const bool both = n_cls > 0 && n_small > 0;
+    cudaStream_t sl = both ? ctx->aux : s;
+    HH_CUDA(cudaEventRecord(ctx->kev[2], s));
+    if (both) {
+        HH_CUDA(cudaEventRecord(ctx->fork_ev, s));
+        HH_CUDA(cudaStreamWaitEvent(sl, ctx->fork_ev, 0));
+    }
     if (n_cls > 0) {
-        HH_CUDA(cudaEventRecord(ctx->kev[0], s));
         for (int i = 0; i < n_cls; ++i) {
             const AcaClass& k = cls[i];
             int64_t stride = (int64_t)k.max_cq * 9 * mr + ceil_div(k.max_cq, (int64_t)sizeof(float));
@@ -410,19 +419,17 @@ void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_par
             const int64_t budget = aca_workspace_budget();
             int64_t teams = std::min<int64_t>(k.end - k.begin, (int64_t)lc.aca_large_cps * ctx->n_sm);
             teams = std::max<int64_t>(1, std::min<int64_t>(teams, budget / (stride * (int64_t)sizeof(float))));
-            float* scratch = dev_alloc_t<float>(stride * teams, s);
-            HH_CUDA(cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), s));
+            float* scratch = dev_alloc_t<float>(stride * teams, sl);
+            HH_CUDA(cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), sl));
             AcaArgs<float> B = A;
             B.work = work_large + k.begin;
             B.n_work = k.end - k.begin;
             B.scratch = scratch;
             B.team_stride = stride;
-            if (ctx->width == 32) launch_tc<32, CtaTeamT<TC_T>>(ctx, B, teams, r.mode, s);
-            else launch_tc<64, CtaTeamT<TC_T>>(ctx, B, teams, r.mode, s);
-            dev_free(scratch, s);
+            if (ctx->width == 32) launch_tc<32, CtaTeamT<TC_T>>(ctx, B, teams, r.mode, sl);
+            else launch_tc<64, CtaTeamT<TC_T>>(ctx, B, teams, r.mode, sl);
+            dev_free(scratch, sl);
         }
-        HH_CUDA(cudaEventRecord(ctx->kev[1], s));
-        ctx->kev_aca_used |= 1;
     }
     if (n_small > 0) {
         constexpr int NT = TC_T / 32;
@@ -437,11 +444,14 @@ void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_par
         B.counter = A.counter + 1;
         B.scratch = scratch;
         B.team_stride = stride;
-        HH_CUDA(cudaEventRecord(ctx->kev[2], s));
         if (ctx->width == 32) launch_tc<32, WarpTeam>(ctx, B, blocks, r.mode, s);
         else launch_tc<64, WarpTeam>(ctx, B, blocks, r.mode, s);
-        HH_CUDA(cudaEventRecord(ctx->kev[3], s));
-        ctx->kev_aca_used |= 2;
         dev_free(scratch, s);
     }
+    if (both) {
+        HH_CUDA(cudaEventRecord(ctx->join_ev, sl));
+        HH_CUDA(cudaStreamWaitEvent(s, ctx->join_ev, 0));
+    }
+    HH_CUDA(cudaEventRecord(ctx->kev[3], s));
+    ctx->kev_aca_used |= 2;
 }

@@ -208,6 +208,9 @@ hh_status hh_create(hh_ctx** out, int device)
         HH_CUDA(cudaMemset(ctx->d_status, 0, sizeof(unsigned)));
         HH_CUDA(cudaMemset(ctx->d_counters, 0, 8 * sizeof(unsigned long long)));
         for (auto& e : ctx->ev) HH_CUDA(cudaEventCreate(&e));
+        HH_CUDA(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+        HH_CUDA(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
+        HH_CUDA(cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming));
         for (auto& e : ctx->kev) HH_CUDA(cudaEventCreate(&e));
         return HH_OK;
     });
@@ -235,6 +238,9 @@ void hh_destroy(hh_ctx* ctx)
     cudaFree(ctx->d_counters);
     for (auto& e : ctx->ev)
         if (e) cudaEventDestroy(e);
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
     for (auto& e : ctx->kev)
         if (e) cudaEventDestroy(e);
     delete ctx;

@@ -30,6 +30,8 @@ struct hh_ctx {
     int kev_near_used = 0;
     unsigned long long launch_base = 0;  // g_hh_launches at the start of the call
     hh_launch_cfg launch{};              // 0 fields: defaults (see resolved_launch)
+    cudaStream_t aux = nullptr;          // second stream: CTA-team ACA classes beside the warp teams
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     // short-range networks (hh_set_short_range): FP32 and FP64 copies
     float* sr_theta_s32 = nullptr;
     float* sr_theta_332 = nullptr;
