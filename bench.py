@@ -33,6 +33,15 @@ cpu_baseline = the FP64 CPU oracle as it stands: 64 sampled rows of the exact
 
 Under torchrun each rank runs its own independent suspension of N particles
 (weak scaling, no collective on the data path); rank 0 prints the line.
+
+--workload selects a further configuration, one line each (1 GPU):
+  batch64      64 suspensions (cubes and Gaussian clouds) in one batched call
+  grad200k     forward U plus the adjoint (dL/dF, dL/dX, dL/dtheta), FP64
+  cube10m      N = 10M uniform cube
+  shortrange1m the headline with the short-range terms of Eq. 6 switched on
+  train        Eq. 5 training steps of the pair MLP
+  filament1m   20k straight chains of 50 beads (bond 2.2a, random
+               orientation) with gravity, bond and bending forces
 """
 from __future__ import annotations
 
@@ -475,6 +484,34 @@ def run_workload(args):
                      "stages_ms": {k: st[k] for k in ("t_tree", "t_part", "t_near", "t_aca", "t_acc")},
                      "rel_err": float(oracle.rel_error(Ud, Uh[rows] - a1 * F[rows])), "rel_err_rows": len(rows),
                      "gpu_launches": launches, "clocks": clocks})
+    elif args.workload == "filament1m":
+        # the filament suspension: straight bead chains (bond 2.2a, random orientation) under gravity;
+        # bead forces from the bond / bending / gravity potentials (straight chains: gravity only)
+        beads = 50
+        nch = max(1, args.n // beads)
+        X, _, side = hh_synth.filaments(nch, beads, seed=1234)
+        n = len(X)
+        phi = n * (4.0 / 3.0) * np.pi / side ** 3
+        F = hh_synth.filament_forces(X, beads)
+        p = hh.Params(leaf_size=args.leaf, eps=args.eps, precision=args.precision)
+        Xd, Fd = torch.as_tensor(X).cuda(), torch.as_tensor(F).cuda()
+        U = torch.empty_like(Xd)
+        total_ms, clocks, launches = _timed(ctx, lambda: ctx.predict(Xd, Fd, p, out=U), args.steps, args.warmup, dev)
+        st = ctx.stats()
+        Uh = U.cpu().numpy()
+        rows = np.sort(np.random.default_rng(0).choice(n, 64, replace=False))
+        Ud = oracle.dense_matvec(X, F, kern, rows=rows, with_self=False)
+        line.update({"metric": "particle-velocities/sec per H-HIGNN prediction, filament suspension",
+                     "value": n * args.steps / (total_ms / 1e3), "unit": "particle-velocities/s",
+                     "ms_per_step": total_ms / args.steps, "dtype": args.precision,
+                     "config": {"workload": f"filaments_{nch}x{beads}_bond2.2a_random_orientation", "n": n,
+                                "chains": nch, "beads": beads, "side": side, "phi": phi,
+                                "forces": "gravity + harmonic bonds (k 100) + bending (kappa 10)",
+                                "leaf_size": args.leaf, "eps": args.eps, "l2": "flushed between steps (256 MB write)"},
+                     "stages_ms": {k: st[k] for k in ("t_tree", "t_part", "t_near", "t_aca", "t_acc")},
+                     "counts": {"n_aca_queries": st["n_aca_queries"], "n_near_pairs": st["n_near_pairs"]},
+                     "rel_err": float(oracle.rel_error(Ud, Uh[rows] - a1 * F[rows])), "rel_err_rows": len(rows),
+                     "gpu_launches": launches, "clocks": clocks})
     print(json.dumps(line), flush=True)
 
 
@@ -491,7 +528,7 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", default="cube1m",
-                    choices=["cube1m", "batch64", "grad200k", "cube10m", "shortrange1m", "train"],
+                    choices=["cube1m", "batch64", "grad200k", "cube10m", "shortrange1m", "train", "filament1m"],
                     help="cube1m is the headline; the others measure further configurations")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))

@@ -16,7 +16,9 @@ synthetic equivalents):
                         rejection; sigma is raised to the smallest value whose
                         peak volume fraction is <= 0.25.
 * ``filaments``      -- straight bead chains at random orientation, placed
-                        without overlap.
+                        without overlap; ``filament_forces`` gives their bead
+                        forces (gravity, harmonic bonds, bending) and
+                        ``perturb`` a displaced variant.
 * ``forces``         -- i.i.d. N(0,1) force components.
 * ``mlp_params``     -- Xavier-uniform weights drawn from SplitMix64, zero
                         biases, every value rounded to bfloat16 so that the
@@ -30,6 +32,7 @@ import numpy as np
 
 __all__ = [
     "cube_side", "rsa_cube", "sigma_min", "gaussian_cloud", "filaments",
+    "filament_energy", "filament_forces", "perturb",
     "forces", "splitmix64", "uniform01", "mlp_params", "mlp_param_count",
     "round_bf16", "GEOMETRY_SEED",
 ]
@@ -150,41 +153,178 @@ def gaussian_cloud(n: int, sigma: float, a: float = 1.0, seed: int = GEOMETRY_SE
 def filaments(n_chains: int, beads: int, bond: float = 2.2, a: float = 1.0, phi: float = 0.1,
               min_gap: float = 2.1, seed: int = GEOMETRY_SEED):
     """Straight chains of ``beads`` beads spaced ``bond`` apart, uniformly random
-    orientation, placed one by one in a cube so that beads of different chains
-    stay >= min_gap apart.  After 1000 consecutive failed placements the cube
-    grows by 5% and placement restarts.  Returns (X, chain_id, side)."""
+    orientation, placed one at a time in a cube (random sequential addition of
+    whole chains) so that beads of different chains stay >= min_gap apart.
+    The cube starts at the side of volume fraction ``phi``.  A chain's start
+    point is uniform over the positions where the whole chain fits in the cube.
+    After 1000 consecutive failed placements the cube grows by 5% in place:
+    the start points of the chains already placed are scaled by 1.05 (a rigid
+    chain then still fits), any bead pair that this brings closer than min_gap
+    (rare) removes the later chain, and placement continues.  Random straight
+    rods this long jam far below phi = 0.1, so the cube grows several times.
+
+    Candidates are drawn in batches of 256 and tested against the placed beads
+    together, then accepted in draw order, each also tested against those of
+    its batch accepted before it; the failure count runs in draw order.
+
+    Beads of chain c are rows c*beads .. c*beads+beads-1, in order along the
+    chain.  Returns (X, chain_id, side); the volume fraction reached is
+    n_chains * beads * (4/3) pi a^3 / side^3.
+
+    Overlap test: a cell grid of side >= min_gap with an empty border layer,
+    so every bead closer than min_gap to a candidate bead sits in one of the
+    27 cells around it; each cell keeps a linked list of its beads."""
     from scipy.spatial import cKDTree
 
     rng = np.random.Generator(np.random.PCG64(seed))
     side = cube_side(n_chains * beads, phi, a)
     offs = np.arange(beads) * bond
+    g2 = min_gap * min_gap
+    nbead = n_chains * beads
+    starts = np.empty((n_chains, 3))
+    dirs = np.empty((n_chains, 3))
+    placed = 0
+
+    def beads_of(st, dv):
+        return (st[:, None, :] + offs[None, :, None] * dv[:, None, :]).reshape(-1, 3)
+
     while True:
-        placed, fails = [], 0
-        tree, tree_n, recent = None, 0, []
-        while len(placed) < n_chains and fails < 1000:
-            v = rng.normal(size=3)
-            v /= np.linalg.norm(v)
-            chain = rng.uniform(0.0, side, size=3)[None, :] + offs[:, None] * v[None, :]
-            ok = not ((chain < 0).any() or (chain > side).any())
-            if ok and tree is not None:
-                d, _ = tree.query(chain, k=1, distance_upper_bound=min_gap)
-                ok = not (d < min_gap).any()
-            if ok and recent:
-                r = np.concatenate(recent)
-                ok = np.min(np.linalg.norm(r[None, :, :] - chain[:, None, :], axis=2)) >= min_gap
-            if not ok:
-                fails += 1
-                continue
-            fails = 0
-            placed.append(chain)
-            recent.append(chain)
-            if len(recent) * beads >= 2048:
-                tree_n = len(placed)
-                tree = cKDTree(np.concatenate(placed[:tree_n]))
-                recent = []
-        if len(placed) == n_chains:
-            return np.ascontiguousarray(np.concatenate(placed)), np.repeat(np.arange(n_chains), beads), side
+        nc = max(1, int(side // min_gap))
+        h = side / nc
+        P = nc + 2
+        stencil = ((np.arange(-1, 2)[:, None, None] * P + np.arange(-1, 2)[None, :, None]) * P
+                   + np.arange(-1, 2)[None, None, :]).ravel()
+
+        def cell_of(x):
+            c = np.clip((x // h).astype(np.int64), 0, nc - 1) + 1
+            return (c[..., 0] * P + c[..., 1]) * P + c[..., 2]
+
+        head = np.full(P * P * P, -1, dtype=np.int64)
+        nxt = np.full(nbead, -1, dtype=np.int64)
+        X = np.empty((nbead, 3))
+        if placed:
+            X[:placed * beads] = beads_of(starts[:placed], dirs[:placed])
+            f = cell_of(X[:placed * beads])
+            order = np.argsort(f, kind="stable")
+            fs = f[order]
+            last = np.r_[fs[1:] != fs[:-1], True]
+            nxt[order[:-1]] = np.where(last[:-1], -1, order[1:])
+            first = np.r_[True, fs[1:] != fs[:-1]]
+            head[fs[first]] = order[first]
+        fails = 0
+        while placed < n_chains and fails < 1000:
+            m = 256
+            V = rng.normal(size=(m, 3))
+            V /= np.linalg.norm(V, axis=1)[:, None]
+            U = rng.uniform(0.0, 1.0, size=(m, 3))
+            E = offs[-1] * V
+            lo = np.maximum(0.0, -E)
+            hi = side - np.maximum(0.0, E)
+            fits = (hi >= lo).all(1)
+            ST = lo + U * (hi - lo)
+            C = ST[:, None, :] + offs[None, :, None] * V[:, None, :]
+            fc = cell_of(C)                                         # [m, beads]
+            idx = head[fc[:, :, None] + stencil[None, None, :]]     # [m, beads, 27]
+            jm, jb, _ = np.nonzero(idx >= 0)
+            idx = idx[idx >= 0]
+            clash = np.zeros(m, dtype=bool)
+            while len(idx):
+                d = X[idx] - C[jm, jb]
+                clash[jm[np.einsum("ij,ij->i", d, d) < g2]] = True
+                idx = nxt[idx]
+                keep = idx >= 0
+                idx, jm, jb = idx[keep], jm[keep], jb[keep]
+            ok = fits & ~clash
+            acc = []
+            for j in range(m):
+                if ok[j] and acc:
+                    Q = C[acc].reshape(-1, 3)
+                    d = Q[:, None, :] - C[j][None, :, :]
+                    ok[j] = not (np.einsum("ijk,ijk->ij", d, d) < g2).any()
+                if not ok[j]:
+                    fails += 1
+                    if fails >= 1000:
+                        break
+                    continue
+                acc.append(j)
+                base = placed * beads
+                X[base:base + beads] = C[j]
+                for k in range(beads):
+                    nxt[base + k] = head[fc[j, k]]
+                    head[fc[j, k]] = base + k
+                starts[placed], dirs[placed] = ST[j], V[j]
+                placed += 1
+                fails = 0
+                if placed == n_chains:
+                    break
+        if placed == n_chains:
+            return X, np.repeat(np.arange(n_chains), beads), side
+        # grow in place; drop the later chain of any pair brought too close
         side *= 1.05
+        starts[:placed] *= 1.05
+        B = beads_of(starts[:placed], dirs[:placed])
+        pr = cKDTree(B).query_pairs(min_gap, output_type="ndarray")
+        if len(pr):
+            pr = pr[pr[:, 0] // beads != pr[:, 1] // beads]
+            if len(pr):
+                d = B[pr[:, 0]] - B[pr[:, 1]]
+                close = np.einsum("ij,ij->i", d, d) < g2
+                drop = np.unique(np.maximum(pr[close, 0], pr[close, 1]) // beads)
+                keep = np.setdiff1d(np.arange(placed), drop)
+                starts[:len(keep)], dirs[:len(keep)] = starts[keep], dirs[keep]
+                placed = len(keep)
+
+
+def perturb(X: np.ndarray, scale: float, seed: int) -> np.ndarray:
+    """X plus i.i.d. N(0, scale^2) displacements (a bent, stretched variant
+    of a chain configuration that exercises the bond and bending forces)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return X + scale * rng.standard_normal(X.shape)
+
+
+def filament_energy(X: np.ndarray, beads: int, k_bond: float = 100.0, l0: float = 2.2,
+                    kappa: float = 10.0, g=(0.0, 0.0, -1.0)) -> float:
+    """Potential energy of chains of ``beads`` consecutive rows (the paper's
+    filament application, Section 4, with explicit potentials): harmonic
+    bonds (k/2)(|r| - l0)^2 over consecutive beads (Eq. 12's spring),
+    bending kappa (1 - t_a . t_b) over consecutive unit bond tangents, and a
+    uniform external force g on every bead (energy -g . x)."""
+    C = X.reshape(-1, beads, 3)
+    r = C[:, 1:] - C[:, :-1]
+    L = np.linalg.norm(r, axis=2)
+    e = 0.5 * k_bond * np.sum((L - l0) ** 2)
+    t = r / L[..., None]
+    e += kappa * np.sum(1.0 - np.sum(t[:, 1:] * t[:, :-1], axis=2))
+    return float(e - np.sum(X @ np.asarray(g, dtype=np.float64)))
+
+
+def filament_forces(X: np.ndarray, beads: int, k_bond: float = 100.0, l0: float = 2.2,
+                    kappa: float = 10.0, g=(0.0, 0.0, -1.0)) -> np.ndarray:
+    """Bead forces F = -grad filament_energy: gravity g on every bead, plus
+    the bond and bending forces of each chain.  These are the forces that the
+    mobility product turns into velocities in the filament suspension; they
+    are inputs of the product, not part of it.
+
+    With r_j = x_{j+1} - x_j, L_j = |r_j|, t_j = r_j / L_j:
+      bond:  dE/dr_j = k (L_j - l0) t_j
+      bend:  d(t_a . t_b)/dr_a = (t_b - (t_a . t_b) t_a) / L_a
+    and dE/dx_{j+1} += dE/dr_j, dE/dx_j -= dE/dr_j."""
+    C = X.reshape(-1, beads, 3)
+    r = C[:, 1:] - C[:, :-1]
+    L = np.linalg.norm(r, axis=2)
+    t = r / L[..., None]
+    dr = k_bond * (L - l0)[..., None] * t                      # dE/dr_j, bonds
+    if beads > 2:
+        ta, tb = t[:, :-1], t[:, 1:]
+        c = np.sum(ta * tb, axis=2)[..., None]
+        dr[:, :-1] -= kappa * (tb - c * ta) / L[:, :-1, None]   # E_bend = kappa (1 - t_a . t_b)
+        dr[:, 1:] -= kappa * (ta - c * tb) / L[:, 1:, None]
+    dE = np.zeros_like(C)
+    dE[:, 1:] += dr
+    dE[:, :-1] -= dr
+    F = -dE.reshape(-1, 3)
+    F += np.asarray(g, dtype=np.float64)[None, :]
+    return F
 
 
 def two_particle_samples(batch: int, seed: int, dmin: float = 2.0, dmax: float = 1000.0):

@@ -411,6 +411,23 @@ void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_par
         HH_CUDA(cudaEventRecord(ctx->fork_ev, s));
         HH_CUDA(cudaStreamWaitEvent(sl, ctx->fork_ev, 0));
     }
+    // joins the second stream back even when an error unwinds from here, so
+    // the caller's stream-ordered frees never overtake a launch still in flight
+    struct Join {
+        cudaStream_t from, into;
+        cudaEvent_t ev;
+        bool on;
+        void now()
+        {
+            on = false;
+            HH_CUDA(cudaEventRecord(ev, from));
+            HH_CUDA(cudaStreamWaitEvent(into, ev, 0));
+        }
+        ~Join()
+        {
+            if (on && cudaEventRecord(ev, from) == cudaSuccess) (void)cudaStreamWaitEvent(into, ev, 0);
+        }
+    } join{sl, s, ctx->join_ev, both};
     if (n_cls > 0) {
         for (int i = 0; i < n_cls; ++i) {
             const AcaClass& k = cls[i];
@@ -448,10 +465,7 @@ void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_par
         else launch_tc<64, WarpTeam>(ctx, B, blocks, r.mode, s);
         dev_free(scratch, s);
     }
-    if (both) {
-        HH_CUDA(cudaEventRecord(ctx->join_ev, sl));
-        HH_CUDA(cudaStreamWaitEvent(s, ctx->join_ev, 0));
-    }
+    if (both) join.now();
     HH_CUDA(cudaEventRecord(ctx->kev[3], s));
     ctx->kev_aca_used |= 2;
 }
