@@ -20,7 +20,8 @@ value    = N * K / (sum of CUDA-event times of the K predictions), inputs
 e2e      = same metric through the same call with the inputs in pinned host
            memory: H2D copy of X and F, prediction, D2H copy of U, per step.
 rel_err  = Eq. 11 (M^(t,2) part only) against the FP64 dense oracle on 64
-           sampled target rows.
+           sampled target rows, with a bootstrap 95% interval over the rows
+           (rel_err_ci95); ms_per_step_min is the fastest timed step (rank 0).
 roofline = the ACA team kernels (the dominant stage).  BF16: algorithmic
            tensor-core flops (2 x MACs of the MLP, 4736 per query for width 32)
            / their event time, against the measured sustained bf16 peak
@@ -132,6 +133,17 @@ ACA_TC_DRAM_BYTES_PER_QUERY = 418.0
 
 def aca_traffic(queries):
     return None if ACA_TC_DRAM_BYTES_PER_QUERY is None else ACA_TC_DRAM_BYTES_PER_QUERY * queries
+
+
+def rel_err_ci95(ref, approx, reps=2000, seed=0):
+    """Bootstrap 95% interval of the sampled Eq. 11 error: target rows are
+    resampled with replacement and eps = sqrt(sum |dU_i|^2 / sum |U_i|^2)
+    recomputed per resample."""
+    num = np.sum((np.asarray(approx) - np.asarray(ref)) ** 2, axis=1)
+    den = np.sum(np.asarray(ref) ** 2, axis=1)
+    pick = np.random.default_rng(seed).integers(0, len(num), size=(reps, len(num)))
+    e = np.sqrt(num[pick].sum(1) / den[pick].sum(1))
+    return [float(np.percentile(e, 2.5)), float(np.percentile(e, 97.5))]
 
 
 def weak_scaling_value(n_local, steps, total_ms_local, dist=None, device="cpu"):
@@ -300,7 +312,8 @@ def run_ours(args, rank, world):
                    "eta": 1.0, "eps": args.eps, "max_rank": 48, "precision": prec,
                    "arithmetic": PRECISION_NOTE[prec],
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"independent suspension per GPU"},
-        "rel_err": rel_err, "rel_err_rows": len(idx),
+        "ms_per_step_min": float(np.min(step_ms)),
+        "rel_err": rel_err, "rel_err_rows": len(idx), "rel_err_ci95": rel_err_ci95(Ud, Ug),
         "stages_ms": {k: st[k] for k in ("t_tree", "t_part", "t_near", "t_aca", "t_acc")},
         "counts": {"n_aca_queries": st["n_aca_queries"], "n_near_pairs": st["n_near_pairs"],
                    "n_blocks_G": st["n_blocks_G"], "n_blocks_H": st["n_blocks_H"], "n_nodes": st["n_nodes"]},
@@ -397,7 +410,8 @@ def run_workload(args):
                      "config": {"workload": "batch64_logN_1e3_2e5_cubes_and_gaussian_clouds", "n": n,
                                 "instances": 64, "leaf_size": args.leaf, "eps": args.eps, "launch": tuned,
                                 "l2": "flushed between steps (256 MB write)"},
-                     "rel_err": float(oracle.rel_error(Ud, Uh[rows] - a1 * F[rows])), "gpu_launches": launches,
+                     "rel_err": float(oracle.rel_error(Ud, Uh[rows] - a1 * F[rows])),
+                     "rel_err_ci95": rel_err_ci95(Ud, Uh[rows] - a1 * F[rows]), "gpu_launches": launches,
                      "clocks": clocks})
     elif args.workload == "grad200k":
         n = args.n if args.n != 1_000_000 else 200000
@@ -483,6 +497,7 @@ def run_workload(args):
                                 "eps": args.eps, "device_mem_peak_gb": torch.cuda.max_memory_allocated() / 1e9},
                      "stages_ms": {k: st[k] for k in ("t_tree", "t_part", "t_near", "t_aca", "t_acc")},
                      "rel_err": float(oracle.rel_error(Ud, Uh[rows] - a1 * F[rows])), "rel_err_rows": len(rows),
+                     "rel_err_ci95": rel_err_ci95(Ud, Uh[rows] - a1 * F[rows]),
                      "gpu_launches": launches, "clocks": clocks})
     elif args.workload == "filament1m":
         # the filament suspension: straight bead chains (bond 2.2a, random orientation) under gravity;
@@ -511,6 +526,7 @@ def run_workload(args):
                      "stages_ms": {k: st[k] for k in ("t_tree", "t_part", "t_near", "t_aca", "t_acc")},
                      "counts": {"n_aca_queries": st["n_aca_queries"], "n_near_pairs": st["n_near_pairs"]},
                      "rel_err": float(oracle.rel_error(Ud, Uh[rows] - a1 * F[rows])), "rel_err_rows": len(rows),
+                     "rel_err_ci95": rel_err_ci95(Ud, Uh[rows] - a1 * F[rows]),
                      "gpu_launches": launches, "clocks": clocks})
     print(json.dumps(line), flush=True)
 
