@@ -29,14 +29,20 @@
  *    4 -> w -> w -> w -> 6.
  *  - stream is a cudaStream_t (NULL = legacy default stream).  Work is
  *    enqueued asynchronously; calls that must read a size back from the
- *    GPU synchronise the stream internally (stated per call).
+ *    GPU synchronise the stream internally (stated per call).  The BF16
+ *    ACA (inside hh_aca and hh_predict) forks part of its work onto a
+ *    second stream owned by the context and joins it back with events
+ *    before the call returns, also on an error: everything the call does
+ *    stays ordered on the caller's stream.  A context must therefore not
+ *    be used from two host threads at once.
  *  - Every call returns hh_status.  On an error the outputs are unspecified
  *    and hh_last_error() returns a message.  HH_WARN_RANK_CAP is a warning:
  *    the outputs are valid.
  *  - The library is single-device: every object belongs to the device the
  *    context was created on; calls must be made with that device current.
  *  - The library allocates its temporaries with cudaMallocAsync on the
- *    call's stream from the device's default memory pool.
+ *    call's stream (or the context's second stream, for work forked there)
+ *    from the device's default memory pool.
  */
 #ifndef HHIGNN_H
 #define HHIGNN_H
