@@ -88,13 +88,19 @@ class ClockSampler:
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
+    # where the raw samples go: --clocks-csv, else a temporary file
+    csv_path = None
+
     def __init__(self, index: int):
+        import tempfile
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = ClockSampler.csv_path or os.path.join(tempfile.gettempdir(),
+                                                          f"clocks_bench_{os.getpid()}.csv")
 
     def __enter__(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        if os.path.dirname(self.path):
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
@@ -543,10 +549,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--clocks-csv", default=None,
+                    help="keep the raw nvidia-smi clock samples of the timed region in this file")
     ap.add_argument("--workload", default="cube1m",
                     choices=["cube1m", "batch64", "grad200k", "cube10m", "shortrange1m", "train", "filament1m"],
                     help="cube1m is the headline; the others measure further configurations")
     args = ap.parse_args()
+    if args.clocks_csv:
+        ClockSampler.csv_path = args.clocks_csv
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":
