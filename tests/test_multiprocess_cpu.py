@@ -66,3 +66,19 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_sampled_error_interval():
+    import numpy as np
+
+    import bench
+    import oracle
+    rng = np.random.default_rng(4)
+    ref = rng.standard_normal((64, 3))
+    approx = ref + 1e-3 * rng.standard_normal((64, 3))
+    lo, hi = bench.rel_err_ci95(ref, approx)
+    e = oracle.rel_error(ref, approx)
+    assert lo < e < hi and hi - lo < e
+    # rows with one common relative error give a zero-width interval
+    lo, hi = bench.rel_err_ci95(ref, 1.001 * ref)
+    assert abs(lo - 1e-3) < 1e-12 and abs(hi - 1e-3) < 1e-12
