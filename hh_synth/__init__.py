@@ -16,9 +16,8 @@ synthetic equivalents):
                         rejection; sigma is raised to the smallest value whose
                         peak volume fraction is <= 0.25.
 * ``filaments``      -- straight bead chains at random orientation, placed
-                        without overlap; ``filament_forces`` gives their bead
-                        forces (gravity, harmonic bonds, bending) and
-                        ``perturb`` a displaced variant.
+                        without overlap; ``perturb`` gives a displaced variant
+                        (the bead forces belong to the time step, not here).
 * ``forces``         -- i.i.d. N(0,1) force components.
 * ``mlp_params``     -- Xavier-uniform weights drawn from SplitMix64, zero
                         biases, every value rounded to bfloat16 so that the
@@ -32,7 +31,7 @@ import numpy as np
 
 __all__ = [
     "cube_side", "rsa_cube", "sigma_min", "gaussian_cloud", "filaments",
-    "filament_energy", "filament_forces", "perturb",
+    "perturb",
     "forces", "splitmix64", "uniform01", "mlp_params", "mlp_param_count",
     "round_bf16", "GEOMETRY_SEED",
 ]
@@ -280,51 +279,6 @@ def perturb(X: np.ndarray, scale: float, seed: int) -> np.ndarray:
     of a chain configuration that exercises the bond and bending forces)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return X + scale * rng.standard_normal(X.shape)
-
-
-def filament_energy(X: np.ndarray, beads: int, k_bond: float = 100.0, l0: float = 2.2,
-                    kappa: float = 10.0, g=(0.0, 0.0, -1.0)) -> float:
-    """Potential energy of chains of ``beads`` consecutive rows (the paper's
-    filament application, Section 4, with explicit potentials): harmonic
-    bonds (k/2)(|r| - l0)^2 over consecutive beads (Eq. 12's spring),
-    bending kappa (1 - t_a . t_b) over consecutive unit bond tangents, and a
-    uniform external force g on every bead (energy -g . x)."""
-    C = X.reshape(-1, beads, 3)
-    r = C[:, 1:] - C[:, :-1]
-    L = np.linalg.norm(r, axis=2)
-    e = 0.5 * k_bond * np.sum((L - l0) ** 2)
-    t = r / L[..., None]
-    e += kappa * np.sum(1.0 - np.sum(t[:, 1:] * t[:, :-1], axis=2))
-    return float(e - np.sum(X @ np.asarray(g, dtype=np.float64)))
-
-
-def filament_forces(X: np.ndarray, beads: int, k_bond: float = 100.0, l0: float = 2.2,
-                    kappa: float = 10.0, g=(0.0, 0.0, -1.0)) -> np.ndarray:
-    """Bead forces F = -grad filament_energy: gravity g on every bead, plus
-    the bond and bending forces of each chain.  These are the forces that the
-    mobility product turns into velocities in the filament suspension; they
-    are inputs of the product, not part of it.
-
-    With r_j = x_{j+1} - x_j, L_j = |r_j|, t_j = r_j / L_j:
-      bond:  dE/dr_j = k (L_j - l0) t_j
-      bend:  d(t_a . t_b)/dr_a = (t_b - (t_a . t_b) t_a) / L_a
-    and dE/dx_{j+1} += dE/dr_j, dE/dx_j -= dE/dr_j."""
-    C = X.reshape(-1, beads, 3)
-    r = C[:, 1:] - C[:, :-1]
-    L = np.linalg.norm(r, axis=2)
-    t = r / L[..., None]
-    dr = k_bond * (L - l0)[..., None] * t                      # dE/dr_j, bonds
-    if beads > 2:
-        ta, tb = t[:, :-1], t[:, 1:]
-        c = np.sum(ta * tb, axis=2)[..., None]
-        dr[:, :-1] -= kappa * (tb - c * ta) / L[:, :-1, None]   # E_bend = kappa (1 - t_a . t_b)
-        dr[:, 1:] -= kappa * (ta - c * tb) / L[:, 1:, None]
-    dE = np.zeros_like(C)
-    dE[:, 1:] += dr
-    dE[:, :-1] -= dr
-    F = -dE.reshape(-1, 3)
-    F += np.asarray(g, dtype=np.float64)[None, :]
-    return F
 
 
 def two_particle_samples(batch: int, seed: int, dmin: float = 2.0, dmax: float = 1000.0):

@@ -35,6 +35,10 @@ PINS = {
     "mlp_gen": "equals the pinned 4 -> w -> w -> w -> 6 pair MLP for those sizes",
     "short_range": "constant-output networks against a distance-matrix formulation (numpy); hand-derived "
                    "3-particle cliques; translation invariance; permutation equivariance",
+    "filament_energy": "closed forms: stretched bond, right-angle and folded joints, straight chain under gravity",
+    "filament_forces": "central differences of filament_energy; the two-bead spring; zero net internal force and "
+                       "torque per chain; straight chains at rest length feel gravity only",
+    "euler_step": "composition of filament_forces, hmatvec and x + dt U (each pinned)",
 }
 
 
@@ -102,6 +106,8 @@ def _declare(L):
         "or_num_threads": (_I, []),
         "or_mlp_gen": (None, [_P, _I, _I, _I, _P, _P]),
         "or_short_range": (None, [_I, _P, _P, _P, _I, _P, _I, _D, _D, _P]),
+        "or_filament_energy": (_D, [_I, _I, _P, _D, _D, _D, _P]),
+        "or_filament_forces": (None, [_I, _I, _P, _D, _D, _D, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -337,3 +343,29 @@ def short_range(X, F, theta_s=None, ws=32, theta_3=None, w3=32, rcut=5.0, a=1.0)
     lib().or_short_range(len(X), _ptr(X), _ptr(F), _ptr(ts), ws, _ptr(t3), w3, float(rcut), float(a), _ptr(U))
     return U
 
+
+def filament_energy(X, beads, k=100.0, l0=2.2, kappa=10.0, g=(0.0, 0.0, -1.0)):
+    """Bond + bending + gravity energy of chains of `beads` consecutive rows (FP64)."""
+    X = _f64(X)
+    nch = len(X) // beads if beads > 0 else 0
+    return lib().or_filament_energy(nch, beads, _ptr(X), k, l0, kappa, _ptr(_f64(g)))
+
+
+def filament_forces(X, beads, k=100.0, l0=2.2, kappa=10.0, g=(0.0, 0.0, -1.0)):
+    """Bead forces -grad filament_energy, [n, 3] FP64."""
+    X = _f64(X)
+    nch = len(X) // beads if beads > 0 else 0
+    F = np.zeros_like(X)
+    lib().or_filament_forces(nch, beads, _ptr(X), k, l0, kappa, _ptr(_f64(g)), _ptr(F))
+    return F
+
+
+def euler_step(X, beads, kernel, dt, leaf=32, eta=1.0, eps=1e-4, max_rank=48, k=100.0, l0=2.2, kappa=10.0,
+               g=(0.0, 0.0, -1.0)):
+    """One explicit Euler step of the filament suspension: F = F(X),
+    U = alpha_1 F + M_H F (the oracle's H-matrix product), X + dt U.
+    Returns (X_new, F, U)."""
+    X = _f64(X)
+    F = filament_forces(X, beads, k, l0, kappa, g)
+    U, _ = hmatvec(X, F, kernel, leaf=leaf, eta=eta, eps=eps, max_rank=max_rank)
+    return X + dt * U, F, U

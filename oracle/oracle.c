@@ -24,7 +24,9 @@
  *   - the analytic gradient of L = sum_i w_i . U_i w.r.t. F, X and theta,
  *     and the training loss of Eq. 5 with its gradient and an Adam step;
  *   - the short-range terms M^(s,2), M^(t,3), M^(s,3) of Eq. 6 (Eq. 2 with
- *     the Eq. 4 normalisations) over neighbours within R_cut.
+ *     the Eq. 4 normalisations) over neighbours within R_cut;
+ *   - the bead forces of the filament suspension (bond, bending, gravity;
+ *     Section 4), which the explicit Euler step x <- x + dt U(x, F(x)) uses.
  *
  * Readings of points the paper leaves open are stated where they are used.
  */
@@ -1002,6 +1004,95 @@ int or_hmatvec(int n, const double *X, const double *F, const or_kernel *k, int 
     free(codes); free(sc); free(perm); free(Xs); free(Fs); free(nb); free(ne); free(ch); free(par);
     free(lo); free(hi); free(G); free(H); free(y); free(pofs); free(part);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Filament suspension: bead forces (Section 4's filament application)       */
+/* ------------------------------------------------------------------------ */
+
+/* Chains of `beads` consecutive rows of X.  Energy (reading: the paper's bond
+ * spring of Eq. 12 and a bending term whose printed force is garbled, taken
+ * from the stated potential):
+ *   E = sum_bonds (k/2)(|r| - l0)^2 + sum_joints kappa (1 - t_a . t_b)
+ *       - sum_beads g . x
+ * with r = x_{j+1} - x_j along each chain and t = r / |r|. */
+double or_filament_energy(int n_chains, int beads, const double *X, double k, double l0, double kappa,
+                          const double *g)
+{
+    double e = 0.0;
+    for (int c = 0; c < n_chains; ++c) {
+        const double *x = X + (int64_t)3 * c * beads;
+        for (int j = 0; j + 1 < beads; ++j) {
+            double r[3], L = 0.0;
+            for (int d = 0; d < 3; ++d) { r[d] = x[3 * (j + 1) + d] - x[3 * j + d]; L += r[d] * r[d]; }
+            L = sqrt(L);
+            e += 0.5 * k * (L - l0) * (L - l0);
+        }
+        for (int j = 0; j + 2 < beads; ++j) {
+            double ra[3], rb[3], La = 0.0, Lb = 0.0, dot = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                ra[d] = x[3 * (j + 1) + d] - x[3 * j + d];
+                rb[d] = x[3 * (j + 2) + d] - x[3 * (j + 1) + d];
+                La += ra[d] * ra[d];
+                Lb += rb[d] * rb[d];
+            }
+            La = sqrt(La);
+            Lb = sqrt(Lb);
+            for (int d = 0; d < 3; ++d) dot += (ra[d] / La) * (rb[d] / Lb);
+            e += kappa * (1.0 - dot);
+        }
+    }
+    for (int64_t i = 0; i < (int64_t)n_chains * beads; ++i)
+        for (int d = 0; d < 3; ++d) e -= g[d] * X[3 * i + d];
+    return e;
+}
+
+/* F = -grad E, accumulated term by term: each bond and each joint adds its
+ * equal and opposite contributions to the beads it joins.
+ *   bond:  dE/dr = k (|r| - l0) t
+ *   joint: dE/dr_a = -kappa (t_b - (t_a.t_b) t_a) / |r_a|,
+ *          dE/dr_b = -kappa (t_a - (t_a.t_b) t_b) / |r_b|
+ * and a bond r = x_{j+1} - x_j passes dE/dr to x_{j+1} and -dE/dr to x_j. */
+void or_filament_forces(int n_chains, int beads, const double *X, double k, double l0, double kappa,
+                        const double *g, double *F)
+{
+    for (int64_t i = 0; i < (int64_t)n_chains * beads; ++i)
+        for (int d = 0; d < 3; ++d) F[3 * i + d] = g[d];
+    for (int c = 0; c < n_chains; ++c) {
+        const double *x = X + (int64_t)3 * c * beads;
+        double *f = F + (int64_t)3 * c * beads;
+        for (int j = 0; j + 1 < beads; ++j) {
+            double r[3], L = 0.0;
+            for (int d = 0; d < 3; ++d) { r[d] = x[3 * (j + 1) + d] - x[3 * j + d]; L += r[d] * r[d]; }
+            L = sqrt(L);
+            for (int d = 0; d < 3; ++d) {
+                double dEdr = k * (L - l0) * (r[d] / L);
+                f[3 * (j + 1) + d] -= dEdr;
+                f[3 * j + d] += dEdr;
+            }
+        }
+        for (int j = 0; j + 2 < beads; ++j) {
+            double ta[3], tb[3], La = 0.0, Lb = 0.0, cs = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                ta[d] = x[3 * (j + 1) + d] - x[3 * j + d];
+                tb[d] = x[3 * (j + 2) + d] - x[3 * (j + 1) + d];
+                La += ta[d] * ta[d];
+                Lb += tb[d] * tb[d];
+            }
+            La = sqrt(La);
+            Lb = sqrt(Lb);
+            for (int d = 0; d < 3; ++d) { ta[d] /= La; tb[d] /= Lb; }
+            for (int d = 0; d < 3; ++d) cs += ta[d] * tb[d];
+            for (int d = 0; d < 3; ++d) {
+                double dEa = -kappa * (tb[d] - cs * ta[d]) / La;   /* bond a: x_j -> x_{j+1}     */
+                double dEb = -kappa * (ta[d] - cs * tb[d]) / Lb;   /* bond b: x_{j+1} -> x_{j+2} */
+                f[3 * (j + 1) + d] -= dEa;
+                f[3 * j + d] += dEa;
+                f[3 * (j + 2) + d] -= dEb;
+                f[3 * (j + 1) + d] += dEb;
+            }
+        }
+    }
 }
 
 /* Eq. 11: || a - b ||_2 / || a ||_2 over all components. */

@@ -33,7 +33,7 @@ def test_filaments_against_oracle(ctx, prec, perturbed):
     X, _, _ = hh_synth.filaments(80, 50, seed=21)
     if perturbed:
         X = hh_synth.perturb(X, 0.05, seed=22)
-    F = hh_synth.filament_forces(X, 50)
+    F = oracle.filament_forces(X, 50)
     k = oracle.PairKernel("mlp", THETA, 32)
     p = hh.Params(precision=prec, leaf_size=32)
     U = ctx.predict(cuda(X), cuda(F), p).cpu().numpy()
@@ -49,7 +49,7 @@ def test_filaments_against_oracle(ctx, prec, perturbed):
 def test_filaments_bf16_leaf64_sampled_rows(ctx):
     # the bench's launch configuration (BF16, C_leaf 64) on 600 chains x 50 beads
     X, _, _ = hh_synth.filaments(600, 50, seed=23)
-    F = hh_synth.filament_forces(X, 50)
+    F = oracle.filament_forces(X, 50)
     p = hh.Params(precision="bf16", leaf_size=64)
     U = ctx.predict(cuda(X), cuda(F), p).cpu().numpy()
     U2 = ctx.predict(cuda(X), cuda(F), p).cpu().numpy()

@@ -1,15 +1,17 @@
-"""The filament suspension inputs: chain placement and the bead forces
-(gravity, harmonic bonds, bending) that the mobility product takes as F.
+"""The filament suspension: chain placement (hh_synth) and the oracle's bead
+forces (gravity, harmonic bonds, bending) that the explicit Euler step feeds
+to the mobility product.
 
-The forces are pinned to closed-form energies of hand-built configurations,
-to central differences of the energy, and to the invariants of internal
-forces (zero net force and torque), so a dropped term, a wrong sign or a
-wrong index fails one of them."""
+The oracle's energy is pinned to closed forms of hand-built configurations;
+its forces to central differences of that energy, to the two-bead spring,
+and to the invariants of internal forces (zero net force and torque), so a
+dropped term, a wrong sign or a wrong index fails one of them."""
 import numpy as np
 import pytest
 from scipy.spatial import cKDTree
 
 import hh_synth
+import oracle
 
 G = np.array([0.0, 0.0, -1.0])
 
@@ -45,22 +47,22 @@ def test_box_grows_when_rods_jam():
 def test_energy_closed_forms():
     # two beads stretched to 3.2: bond energy (100/2)(1.0)^2 = 50; gravity -g.x
     X = np.array([[0.0, 0.0, 5.0], [3.2, 0.0, 5.0]])
-    assert hh_synth.filament_energy(X, 2) == pytest.approx(50.0 + 10.0, abs=1e-12)
-    assert hh_synth.filament_energy(X, 2, g=(0, 0, 0)) == pytest.approx(50.0, abs=1e-12)
+    assert oracle.filament_energy(X, 2) == pytest.approx(50.0 + 10.0, abs=1e-12)
+    assert oracle.filament_energy(X, 2, g=(0, 0, 0)) == pytest.approx(50.0, abs=1e-12)
     # three beads at rest length, right angle: bending 10 (1 - cos 90) = 10
     X = np.array([[0.0, 0.0, 0.0], [2.2, 0.0, 0.0], [2.2, 2.2, 0.0]])
-    assert hh_synth.filament_energy(X, 3, g=(0, 0, 0)) == pytest.approx(10.0, abs=1e-12)
+    assert oracle.filament_energy(X, 3, g=(0, 0, 0)) == pytest.approx(10.0, abs=1e-12)
     # folded back on itself: 10 (1 - cos 180) = 20
     X = np.array([[0.0, 0.0, 0.0], [2.2, 0.0, 0.0], [0.0, 0.0, 0.0]])
-    assert hh_synth.filament_energy(X, 3, g=(0, 0, 0)) == pytest.approx(20.0, abs=1e-12)
+    assert oracle.filament_energy(X, 3, g=(0, 0, 0)) == pytest.approx(20.0, abs=1e-12)
     # a straight chain at rest length has only the gravity energy
     X = np.array([[0.0, 0.0, 1.0], [0.0, 0.0, 3.2], [0.0, 0.0, 5.4]])
-    assert hh_synth.filament_energy(X, 3) == pytest.approx(9.6, abs=1e-12)
+    assert oracle.filament_energy(X, 3) == pytest.approx(9.6, abs=1e-12)
 
 
 def test_two_bead_force_is_the_spring():
     X = np.array([[0.0, 0.0, 0.0], [3.0, 4.0, 0.0]])                  # |r| = 5
-    F = hh_synth.filament_forces(X, 2, g=(0, 0, 0))
+    F = oracle.filament_forces(X, 2, g=(0, 0, 0))
     u = np.array([0.6, 0.8, 0.0])
     assert np.allclose(F[1], -100.0 * (5.0 - 2.2) * u, atol=1e-12)    # pulled back
     assert np.allclose(F[0], +100.0 * (5.0 - 2.2) * u, atol=1e-12)
@@ -68,7 +70,7 @@ def test_two_bead_force_is_the_spring():
 
 def test_straight_chains_feel_only_gravity():
     X, _, _ = hh_synth.filaments(30, 50, seed=9)
-    F = hh_synth.filament_forces(X, 50)
+    F = oracle.filament_forces(X, 50)
     assert np.allclose(F, G[None, :], rtol=0, atol=1e-9)
 
 
@@ -76,7 +78,7 @@ def test_straight_chains_feel_only_gravity():
 def test_forces_are_minus_the_energy_gradient(beads):
     X, _, _ = hh_synth.filaments(3, beads, seed=11)
     X = hh_synth.perturb(X, 0.3, seed=12)
-    F = hh_synth.filament_forces(X, beads)
+    F = oracle.filament_forces(X, beads)
     h = 1e-6
     Fd = np.empty_like(X)
     for i in range(X.shape[0]):
@@ -84,17 +86,28 @@ def test_forces_are_minus_the_energy_gradient(beads):
             Xp, Xm = X.copy(), X.copy()
             Xp[i, c] += h
             Xm[i, c] -= h
-            Fd[i, c] = -(hh_synth.filament_energy(Xp, beads) - hh_synth.filament_energy(Xm, beads)) / (2 * h)
+            Fd[i, c] = -(oracle.filament_energy(Xp, beads) - oracle.filament_energy(Xm, beads)) / (2 * h)
     assert np.max(np.abs(F - Fd)) <= 1e-6 * np.max(np.abs(F))
 
 
 def test_internal_forces_have_no_net_force_or_torque():
     X, _, _ = hh_synth.filaments(20, 9, seed=13)
     X = hh_synth.perturb(X, 0.2, seed=14)
-    Fi = hh_synth.filament_forces(X, 9) - G[None, :]
+    Fi = oracle.filament_forces(X, 9) - G[None, :]
     scale = np.abs(Fi).max() * len(X)
     for c in range(20):
         s = slice(9 * c, 9 * c + 9)
         assert np.abs(Fi[s].sum(axis=0)).max() <= 1e-12 * scale
         assert np.abs(np.cross(X[s], Fi[s]).sum(axis=0)).max() <= 1e-10 * scale * np.abs(X).max()
     assert np.abs(Fi).max() > 1.0                                      # the perturbation is felt
+
+
+def test_euler_step_composes_its_parts():
+    X, _, _ = hh_synth.filaments(6, 8, seed=15)
+    X = hh_synth.perturb(X, 0.1, seed=16)
+    k = oracle.PairKernel("mlp", hh_synth.mlp_params(32, 7), 32)
+    X1, F, U = oracle.euler_step(X, 8, k, 0.01)
+    assert np.array_equal(F, oracle.filament_forces(X, 8))
+    Ud = oracle.dense_matvec(X, F, k)                       # nothing admissible at 48 beads: exact
+    assert oracle.rel_error(Ud, U) < 1e-13
+    assert np.allclose(X1, X + 0.01 * U, rtol=0, atol=1e-15)
