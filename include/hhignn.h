@@ -150,7 +150,7 @@ hh_status hh_matvec(hh_ctx *ctx, const hh_hmat *h, const double *F_dev, double *
 /* One prediction U = M(X) F end to end (tree, partition, ACA fused with the
  * low-rank apply, inadmissible blocks, FP64 accumulation) without keeping
  * the factors: each admissible block's C and Q live only in a bounded
- * per-team workspace.  This is the per-time-step call of Section 2.4.
+ * per-team workspace.  This is the per-time-step call of Section 2.5.
  * X_dev, F_dev, U_dev: [N, 3] FP64 device, N = offsets[batch].  Synchronises
  * as hh_build_tree and hh_partition do. */
 hh_status hh_predict(hh_ctx *ctx, const double *X_dev, const double *F_dev, const int64_t *offsets,
@@ -318,6 +318,42 @@ hh_status hh_get_launch(hh_ctx *ctx, hh_launch_cfg *cfg);
  * per-block partial sums (none: each block's output is written once). */
 hh_status hh_autotune(hh_ctx *ctx, const double *X_dev, const int64_t *offsets, int32_t batch, const hh_params *p,
                       int32_t reps, void *stream, hh_launch_cfg *best);
+
+/* Filament suspension (the paper's filament application, Section 4.3).
+ * Chains are `beads` consecutive rows of X (chain c = rows c*beads ..
+ * c*beads + beads - 1, in order along the chain).  With r = x_{j+1} - x_j
+ * and t = r / |r| along a chain, the bead forces are F = -grad E of
+ *   E = sum_bonds (k_bond/2)(|r| - l0)^2            (the bond spring of Eq. 12)
+ *     + sum_joints kappa (1 - t_j . t_{j+1})        (bending)
+ *     - sum_beads g . x                             (uniform body force)
+ * The paper prints a bending force whose form is garbled; this potential's
+ * gradient is used instead. */
+typedef struct {
+    double k_bond;   /* bond stiffness k (100 in the 1M-bead suspension)   */
+    double l0;       /* bond rest length (2.2 a)                            */
+    double kappa;    /* bending stiffness (10)                              */
+    double g[3];     /* force on every bead, e.g. gravity (0, 0, -1)        */
+} hh_filament_params;
+
+/* F_dev [n_chains * beads, 3] FP64 device (caller-owned) = the bead forces
+ * above for X_dev (same layout).  n_chains >= 0, beads >= 1 (a one-bead
+ * chain feels g only), n_chains * beads < 2^31.  A zero-length bond or a
+ * non-finite result gives HH_ERR_NUMERIC (F then unspecified).
+ * Synchronises the stream (status read-back). */
+hh_status hh_filament_forces(hh_ctx *ctx, const double *X_dev, int64_t n_chains, int32_t beads,
+                             const hh_filament_params *fp, void *stream, double *F_dev);
+
+/* One explicit Euler step of the filament suspension (Section 2.5's time
+ * step with the forces of Section 4.3's filaments), in place on X_dev:
+ *   F = hh_filament_forces(X);  U = alpha_1 F + M_H(X) F  (hh_predict under p,
+ *   one suspension);  X <- X + dt U.
+ * F_dev and U_dev ([N, 3] FP64 device, caller-owned) receive the step's F
+ * and U.  n_chains >= 1.  Errors as hh_filament_forces and hh_predict; on
+ * an error X is unchanged.  HH_WARN_RANK_CAP from the prediction is passed
+ * on (X is updated).  Synchronises as hh_predict does. */
+hh_status hh_filament_step(hh_ctx *ctx, double *X_dev, int64_t n_chains, int32_t beads,
+                           const hh_filament_params *fp, const hh_params *p, double dt, void *stream,
+                           double *F_dev, double *U_dev);
 
 void hh_tree_free(hh_tree *t);
 void hh_blocks_free(hh_blocks *b);

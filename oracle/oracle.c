@@ -26,7 +26,8 @@
  *   - the short-range terms M^(s,2), M^(t,3), M^(s,3) of Eq. 6 (Eq. 2 with
  *     the Eq. 4 normalisations) over neighbours within R_cut;
  *   - the bead forces of the filament suspension (bond, bending, gravity;
- *     Section 4), which the explicit Euler step x <- x + dt U(x, F(x)) uses.
+ *     Section 4.3), which the explicit Euler step x <- x + dt U(x, F(x)) of
+ *     Section 2.5 uses.
  *
  * Readings of points the paper leaves open are stated where they are used.
  */
@@ -1007,7 +1008,7 @@ int or_hmatvec(int n, const double *X, const double *F, const or_kernel *k, int 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Filament suspension: bead forces (Section 4's filament application)       */
+/* Filament suspension: bead forces (Section 4.3, filament application)    */
 /* ------------------------------------------------------------------------ */
 
 /* Chains of `beads` consecutive rows of X.  Energy (reading: the paper's bond

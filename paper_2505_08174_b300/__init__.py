@@ -35,6 +35,7 @@ EXPORTS = [
     "hh_export_blocks", "hh_export_aca", "hh_stats", "hh_tree_free", "hh_blocks_free", "hh_hmat_free",
     "hh_aca_block_apply_noalloc", "hh_eval_pairs", "hh_train_loss_grad", "hh_train_step",
     "hh_set_launch", "hh_get_launch", "hh_autotune", "hh_set_short_range", "hh_short_range",
+    "hh_filament_forces", "hh_filament_step",
 ]
 
 
@@ -68,6 +69,16 @@ class CLaunch(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class CFilament(ctypes.Structure):
+    """hh_filament_params: bond spring, rest length, bending stiffness, body force."""
+    _fields_ = [("k_bond", ctypes.c_double), ("l0", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("g", ctypes.c_double * 3)]
+
+
+def Filament(k_bond=100.0, l0=2.2, kappa=10.0, g=(0.0, 0.0, -1.0)) -> CFilament:
+    return CFilament(float(k_bond), float(l0), float(kappa), (ctypes.c_double * 3)(*[float(v) for v in g]))
 
 
 _P = ctypes.c_void_p
@@ -111,6 +122,8 @@ def lib():
             "hh_autotune": (st, [_P, _P, _P, i32, _P, i32, _P, _P]),
             "hh_set_short_range": (st, [_P, _P, _P, ctypes.c_int, ctypes.c_double, _P]),
             "hh_short_range": (st, [_P, _P, _P, _P, i32, _P, _P, _P]),
+            "hh_filament_forces": (st, [_P, _P, ctypes.c_int64, i32, _P, _P, _P]),
+            "hh_filament_step": (st, [_P, _P, ctypes.c_int64, i32, _P, _P, ctypes.c_double, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -248,6 +261,33 @@ class Context:
         self._check(lib().hh_short_range(self._h, _dptr(X), _dptr(F), off.ctypes.data_as(_P), len(off) - 1,
                                          ctypes.byref(params), _stream(stream), _dptr(U)), "hh_short_range")
         return U
+
+    # -- filament suspension: bead forces and the explicit Euler step -------------
+    def filament_forces(self, X, beads, fil: CFilament = None, out=None, stream=None):
+        """Bead forces of chains of `beads` consecutive rows of X (bond, bending, body force)."""
+        import torch
+        _check_xyz(X, "X")
+        if beads < 1 or X.shape[0] % beads:
+            raise ValueError("X must hold whole chains of `beads` rows")
+        fil = Filament() if fil is None else fil
+        F = torch.empty_like(X) if out is None else out
+        self._check(lib().hh_filament_forces(self._h, _dptr(X), X.shape[0] // beads, int(beads), ctypes.byref(fil),
+                                             _stream(stream), _dptr(F)), "hh_filament_forces")
+        return F
+
+    def filament_step(self, X, beads, params: CParams, dt, fil: CFilament = None, F=None, U=None, stream=None):
+        """One explicit Euler step in place on X: F = forces(X), U = M(X) F, X += dt U.  Returns (F, U)."""
+        import torch
+        _check_xyz(X, "X")
+        if beads < 1 or X.shape[0] % beads:
+            raise ValueError("X must hold whole chains of `beads` rows")
+        fil = Filament() if fil is None else fil
+        F = torch.empty_like(X) if F is None else F
+        U = torch.empty_like(X) if U is None else U
+        st = lib().hh_filament_step(self._h, _dptr(X), X.shape[0] // beads, int(beads), ctypes.byref(fil),
+                                    ctypes.byref(params), float(dt), _stream(stream), _dptr(F), _dptr(U))
+        self.last_status = self._check(st, "hh_filament_step")
+        return F, U
 
     # -- launch shape and autotuner ---------------------------------------------
     def set_launch(self, small_max=0, aca_small_cps=0, aca_large_cps=0, near_cps=0):

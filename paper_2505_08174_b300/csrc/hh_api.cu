@@ -844,3 +844,70 @@ void hh_blocks_free(hh_blocks* b) { free_blocks(b); }
 void hh_hmat_free(hh_hmat* h) { free_hmat(h); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Filament suspension: bead forces and the explicit Euler step
+// ---------------------------------------------------------------------------
+namespace {
+
+FilamentArgs filament_args(const hh_filament_params* fp)
+{
+    HH_REQUIRE(fp != nullptr, HH_ERR_ARG, "NULL filament parameters");
+    FilamentArgs a{fp->k_bond, fp->l0, fp->kappa, {fp->g[0], fp->g[1], fp->g[2]}};
+    bool fin = std::isfinite(a.k) && std::isfinite(a.l0) && std::isfinite(a.kappa);
+    for (double v : a.g) fin = fin && std::isfinite(v);
+    HH_REQUIRE(fin, HH_ERR_ARG, "filament parameters must be finite");
+    return a;
+}
+
+void check_chains(int64_t n_chains, int32_t beads)
+{
+    HH_REQUIRE(n_chains >= 0 && beads >= 1, HH_ERR_ARG, "need n_chains >= 0 and beads >= 1");
+    HH_REQUIRE(n_chains <= (int64_t)INT32_MAX / beads, HH_ERR_ARG, "n_chains * beads exceeds 2^31 - 1");
+}
+
+}  // namespace
+
+hh_status hh_filament_forces(hh_ctx* ctx, const double* X_dev, int64_t n_chains, int32_t beads,
+                             const hh_filament_params* fp, void* stream, double* F_dev)
+{
+    if (!ctx) return HH_ERR_ARG;
+    return guarded(ctx, [&]() {
+        check_chains(n_chains, beads);
+        const FilamentArgs a = filament_args(fp);
+        HH_REQUIRE(n_chains == 0 || (X_dev && F_dev), HH_ERR_ARG, "NULL argument");
+        cudaStream_t s = (cudaStream_t)stream;
+        reset_call(ctx, s);
+        filament_forces_launch(ctx, X_dev, n_chains, beads, a, F_dev, s);
+        return read_status(ctx, s);
+    });
+}
+
+hh_status hh_filament_step(hh_ctx* ctx, double* X_dev, int64_t n_chains, int32_t beads, const hh_filament_params* fp,
+                           const hh_params* p, double dt, void* stream, double* F_dev, double* U_dev)
+{
+    if (!ctx) return HH_ERR_ARG;
+    const unsigned long long base = g_hh_launches;   // the step's launches, forces through update
+    hh_status st = guarded(ctx, [&]() {
+        check_chains(n_chains, beads);
+        const FilamentArgs a = filament_args(fp);
+        check_params(ctx, p);
+        HH_REQUIRE(std::isfinite(dt), HH_ERR_ARG, "dt must be finite");
+        HH_REQUIRE(n_chains >= 1, HH_ERR_ARG, "need at least one chain");
+        HH_REQUIRE(X_dev && F_dev && U_dev, HH_ERR_ARG, "NULL argument");
+        cudaStream_t s = (cudaStream_t)stream;
+        reset_call(ctx, s);
+        filament_forces_launch(ctx, X_dev, n_chains, beads, a, F_dev, s);
+        return read_status(ctx, s);
+    });
+    if (st != HH_OK) return st;
+    const int64_t offsets[2] = {0, n_chains * beads};
+    st = hh_predict(ctx, X_dev, F_dev, offsets, 1, p, stream, U_dev);
+    if (st != HH_OK && st != HH_WARN_RANK_CAP) return st;
+    const hh_status st2 = guarded(ctx, [&]() {
+        euler_launch(X_dev, U_dev, 3 * n_chains * beads, dt, (cudaStream_t)stream);
+        return HH_OK;
+    });
+    ctx->stats.n_launches = (int64_t)(g_hh_launches - base);
+    return st2 != HH_OK ? st2 : st;
+}

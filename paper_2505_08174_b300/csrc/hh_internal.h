@@ -233,3 +233,12 @@ inline const R* theta_for(const hh_ctx* ctx, const hh_params& p, int* n)
 
 inline int real_bytes(const hh_params& p) { return p.precision == HH_FP64 ? 8 : 4; }
 inline int kernel_kind(const hh_params& p, int width) { return p.kernel == HH_RPY ? 2 : (width == 64 ? 1 : 0); }
+
+// Filament suspension (hh_step.cu): bead forces of the chain potentials and
+// the Euler update X += dt U.
+struct FilamentArgs {
+    double k, l0, kappa, g[3];
+};
+void filament_forces_launch(hh_ctx* ctx, const double* X, int64_t n_chains, int32_t beads, const FilamentArgs& a,
+                            double* F, cudaStream_t s);
+void euler_launch(double* X, const double* U, int64_t n3, double dt, cudaStream_t s);
