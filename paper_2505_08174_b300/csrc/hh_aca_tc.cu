@@ -17,6 +17,13 @@
 //     columns per round, and meet only at the end of each pass.
 // A team whose pass is complete does its pivot / Gram / stopping work before
 // its next round.
+//
+// Launches: one warp-team launch over the small blocks on the caller's
+// stream, and one CTA-team launch per size class of the large blocks on the
+// context's second stream, forked from and joined back to the caller's
+// stream by events.  The two run concurrently, so the serial tails of the
+// few largest blocks overlap with the bulk of the small ones.  Each block
+// writes its own outputs, and each launch has its own work counter.
 #include <algorithm>
 
 #include "hh_aca.cuh"
