@@ -248,7 +248,8 @@ typedef struct {
     int64_t rank_hist[65];  /* rank_hist[min(rank, 64)] (hh_aca only)        */
     double t_kernel_aca;    /* ms inside the ACA team kernels (CUDA events)   */
     double t_kernel_near;   /* ms inside the near-field kernel (CUDA events)  */
-    int64_t n_launches;     /* kernels this library launched in the call      */
+    int64_t n_launches;     /* kernels this library launched in the call
+                               (hh_filament_step: the whole step)            */
     double t_short;         /* ms of the short-range terms (0 when off)       */
     int64_t n_short_pairs;  /* neighbour pairs within R_cut (directed)        */
 } hh_stats_t;
@@ -278,7 +279,7 @@ hh_status hh_set_short_range(hh_ctx *ctx, const float *theta_s_dev, const float 
 hh_status hh_short_range(hh_ctx *ctx, const double *X_dev, const double *F_dev, const int64_t *offsets,
                          int32_t batch, const hh_params *p, void *stream, double *U_dev);
 
-/* Counters of the last hh_predict / hh_aca on ctx. */
+/* Counters of the last hh_predict / hh_aca / hh_filament_step on ctx. */
 hh_status hh_stats(hh_ctx *ctx, hh_stats_t *out);
 
 /* Launch shape of the block-ACA and near-field kernels (the paper fixes
