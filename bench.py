@@ -320,6 +320,8 @@ def run_ours(args, rank, world):
                    "arithmetic": PRECISION_NOTE[prec],
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"independent suspension per GPU"},
         "ms_per_step_min": float(np.min(step_ms)),
+        "device_mem_gb": {"library_peak": st.get("mem_peak_bytes", -1) / 1e9,
+                          "torch_peak": torch.cuda.max_memory_allocated() / 1e9},
         "rel_err": rel_err, "rel_err_rows": len(idx), "rel_err_ci95": rel_err_ci95(Ud, Ug),
         "stages_ms": {k: st[k] for k in ("t_tree", "t_part", "t_near", "t_aca", "t_acc")},
         "counts": {"n_aca_queries": st["n_aca_queries"], "n_near_pairs": st["n_near_pairs"],
@@ -501,7 +503,8 @@ def run_workload(args):
                      "value": n * args.steps / (total_ms / 1e3), "unit": "particle-velocities/s",
                      "ms_per_step": total_ms / args.steps, "dtype": args.precision,
                      "config": {"workload": "uniform_cube_rsa_N10000000_phi0.1", "n": n, "leaf_size": args.leaf,
-                                "eps": args.eps, "device_mem_peak_gb": torch.cuda.max_memory_allocated() / 1e9},
+                                "eps": args.eps, "device_mem_peak_gb": torch.cuda.max_memory_allocated() / 1e9,
+                                "library_mem_peak_gb": st.get("mem_peak_bytes", -1) / 1e9},
                      "stages_ms": {k: st[k] for k in ("t_tree", "t_part", "t_near", "t_aca", "t_acc")},
                      "rel_err": float(oracle.rel_error(Ud, Uh[rows] - a1 * F[rows])), "rel_err_rows": len(rows),
                      "rel_err_ci95": rel_err_ci95(Ud, Uh[rows] - a1 * F[rows]),

@@ -252,6 +252,11 @@ typedef struct {
                                (hh_filament_step: the whole step)            */
     double t_short;         /* ms of the short-range terms (0 when off)       */
     int64_t n_short_pairs;  /* neighbour pairs within R_cut (directed)        */
+    int64_t mem_peak_bytes; /* high-water mark of the device's default memory
+                               pool during the call: the library's stream-
+                               ordered temporaries (plus any other user of
+                               that pool); -1 if the driver does not report
+                               it                                            */
 } hh_stats_t;
 
 /* Short-range networks of Eq. 6 (Eq. 2 with the Eq. 4 normalisations; the

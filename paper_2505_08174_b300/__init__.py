@@ -60,7 +60,7 @@ class CStats(ctypes.Structure):
                 ("n_blocks_G", ctypes.c_int64), ("n_blocks_H", ctypes.c_int64), ("n_nodes", ctypes.c_int64),
                 ("rank_hist", ctypes.c_int64 * 65), ("t_kernel_aca", ctypes.c_double),
                 ("t_kernel_near", ctypes.c_double), ("n_launches", ctypes.c_int64), ("t_short", ctypes.c_double),
-                ("n_short_pairs", ctypes.c_int64)]
+                ("n_short_pairs", ctypes.c_int64), ("mem_peak_bytes", ctypes.c_int64)]
 
 
 class CLaunch(ctypes.Structure):

@@ -100,8 +100,33 @@ hh_status guarded(hh_ctx* ctx, F&& f)
     }
 }
 
+// The default memory pool's high-water mark (the library's stream-ordered
+// temporaries), reset at the start of a call and read at its end.  Failures
+// are not errors of the call: the mark is then reported as -1.
+void mem_mark_reset(hh_ctx* ctx)
+{
+    cudaMemPool_t pool;
+    uint64_t zero = 0;
+    if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) != cudaSuccess ||
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero) != cudaSuccess)
+        (void)cudaGetLastError();
+}
+
+int64_t mem_mark_read(hh_ctx* ctx)
+{
+    cudaMemPool_t pool;
+    uint64_t high = 0;
+    if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return -1;
+    }
+    return (int64_t)high;
+}
+
 void reset_call(hh_ctx* ctx, cudaStream_t s)
 {
+    mem_mark_reset(ctx);
     HH_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s));
     HH_CUDA(cudaMemsetAsync(ctx->d_counters, 0, 8 * sizeof(unsigned long long), s));
     ctx->last_stream = s;
@@ -124,6 +149,7 @@ void finish_stats(hh_ctx* ctx)
         ctx->stats.t_kernel_near = ms;
     }
     ctx->stats.n_launches = (int64_t)(g_hh_launches - ctx->launch_base);
+    ctx->stats.mem_peak_bytes = mem_mark_read(ctx);
 }
 
 hh_status read_status(hh_ctx* ctx, cudaStream_t s)
