@@ -10,6 +10,9 @@ import paper_2505_08174_b300 as hh  # noqa: E402
 
 
 def test_peak_memory_is_reported():
+    import gc
+    gc.collect()                      # structures of earlier tests are freed before the marks are taken
+    torch.cuda.synchronize()
     c = hh.Context()
     c.set_mlp(hh_synth.mlp_params(32, 7), 32)
     total = torch.cuda.get_device_properties(0).total_memory
