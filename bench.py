@@ -44,6 +44,9 @@ Under torchrun each rank runs its own independent suspension of N particles
   filament1m   20k straight chains of 50 beads (bond 2.2a, random
                orientation), explicit Euler steps: GPU bead forces (gravity,
                bonds, bending), prediction, position update
+  peaks        throughput of the units the pair-kernel MLP leans on (MUFU
+               ex2 / rcp / tanh, FP32 and FP64 FMA, the epilogue SiLU), with
+               the SM clock sampled meanwhile
 """
 from __future__ import annotations
 
@@ -384,6 +387,15 @@ def _timed(ctx, call, steps, warmup, dev):
     return float(np.sum(ms)), clk.summary(), launches
 
 
+def measure_units(ctx, iters=1 << 17):
+    """Measured rates (ops/s) of the arithmetic units of the activation-bound
+    MLP (hh_probe_throughput), each timed over ~0.1-1 s."""
+    out = {}
+    for k, scale in (("mufu_ex2", 1), ("mufu_rcp", 1), ("mufu_tanh", 1), ("silu", 1), ("ffma", 8), ("dfma", 1)):
+        out[k] = ctx.probe(k, iters * scale)
+    return out
+
+
 def run_workload(args):
     import torch
 
@@ -400,7 +412,14 @@ def run_workload(args):
     a1 = oracle.self_mobility()
     line = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "data": "synthetic"}
-    if args.workload == "batch64":
+    if args.workload == "peaks":
+        with ClockSampler(dev) as clk:
+            rates = measure_units(ctx)
+        line.update({"metric": "arithmetic-unit throughput (MUFU, FMA) on one B300",
+                     "value": rates["silu"], "unit": "SiLU/s", "ms_per_step": None, "dtype": "f32",
+                     "config": {"workload": "unit_probes_8chains_8x256_threads_per_sm"},
+                     "rates_per_s": rates, "gpu_launches": 12, "clocks": clk.summary()})
+    elif args.workload == "batch64":
         X, off = batch64_inputs()
         n = len(X)
         F = hh_synth.forces(n, 0)
@@ -566,7 +585,7 @@ def main():
     ap.add_argument("--clocks-csv", default=None,
                     help="keep the raw nvidia-smi clock samples of the timed region in this file")
     ap.add_argument("--workload", default="cube1m",
-                    choices=["cube1m", "batch64", "grad200k", "cube10m", "shortrange1m", "train", "filament1m"],
+                    choices=["cube1m", "batch64", "grad200k", "cube10m", "shortrange1m", "train", "filament1m", "peaks"],
                     help="cube1m is the headline; the others measure further configurations")
     args = ap.parse_args()
     if args.clocks_csv:

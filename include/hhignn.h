@@ -184,21 +184,38 @@ hh_status hh_train_step(hh_ctx *ctx, float *theta_dev, float *m_dev, float *v_de
                         const double *r_dev, const double *e_dev, const double *U_dev, int64_t batch,
                         double radius, double lr, void *stream, double *loss);
 
-/* Allocation-free product of one block (the paper has no counterpart; it is
- * a service for callers that may not allocate device memory when they call,
- * e.g. an application whose device memory is all handed to its own pool, or
- * a real-time step that must not risk the synchronisation or failure of a
- * cudaMalloc).  y_dev [c, 3] FP64 = C (Q F) where C Q is the Algorithm 2
- * approximation (p->eps, p->max_rank, p->j1_rule, p->precision, p->kernel) of
- * the block G(m, n) = K(Xt_m - Xs_n); Xt_dev [c, 3], Xs_dev [q, 3], F_dev
- * [q, 3] FP64 device, caller-owned; rank_dev (int32, may be NULL) receives the
- * rank.  1 <= c, q <= 128 and max_rank <= 64, else HH_ERR_ARG.  Every
- * temporary lives in one fixed 1.2 MB device array inside the library, held
- * by every GPU that loads it until exit: the call allocates nothing.  The
- * first call on a device looks up that array's address (make it before any
- * stream capture).  Calls share the array: two calls that overlap on the GPU
- * race.  ctx must have been created (and hh_set_mlp called for the MLP
- * kernel) beforehand; the call is asynchronous on stream. */
+/* Throughput probe of one arithmetic unit (measurement support for the
+ * roofline of the activation-bound pair-kernel MLP; the paper has no
+ * counterpart).  kind: 0 MUFU ex2.approx.f32, 1 MUFU rcp.approx.f32, 2 MUFU
+ * tanh.approx.f32, 3 FP32 FMA, 4 FP64 FMA, 5 the SiLU of the tensor-core
+ * epilogues (bias add, one ex2 and one rcp).  Runs iters dependent steps of 8
+ * independent chains per thread on 8 CTAs x 256 threads per SM, timed with
+ * CUDA events on stream; *ops_per_s receives operations per second (one FMA,
+ * one MUFU op or one SiLU each).  Synchronises the stream.  HH_ERR_ARG for
+ * kind outside [0, 5] or iters outside [1, 2^30]. */
+hh_status hh_probe_throughput(hh_ctx *ctx, int32_t kind, int64_t iters, void *stream, double *ops_per_s);
+
+/* Allocation-free product of one block.  The paper has no counterpart: this
+ * is a service for callers that may not allocate device memory when they
+ * call -- an application whose device memory is all handed to its own pool,
+ * or a real-time step that must not risk the synchronisation or the failure
+ * of a cudaMalloc.  y_dev [c, 3] FP64 = C (Q F), where C Q is the block
+ * approximation hh_aca computes (same pivot and stopping rules; p->eps,
+ * p->max_rank, p->j1_rule, p->kernel) of the block G(m, n) = K(Xt_m - Xs_n),
+ * run by the SIMT kernels: p->precision HH_FP64 or HH_FP32 (HH_BF16 is
+ * rejected with HH_ERR_ARG).  Xt_dev [c, 3], Xs_dev [q, 3], F_dev [q, 3]
+ * FP64 device, caller-owned; rank_dev (int32, may be NULL) receives the rank
+ * (rank == max_rank < min(c, q) means the block stopped at the rank cap;
+ * this call returns HH_OK then, as it returns before the GPU has run).
+ * 1 <= c, q <= 128 and max_rank <= 64, else HH_ERR_ARG; the current device
+ * must be ctx's, else HH_ERR_ARG.  Every temporary lives in one fixed
+ * 1,195,264-byte device array inside the library, held by every GPU that
+ * loads it until exit: the call allocates nothing.  Each call looks up that
+ * array's address on the current device; the first call on a device may load
+ * the library's device code there, so make it before any stream capture.
+ * Calls share the array: two calls that overlap on the GPU race.  ctx must
+ * have been created (and hh_set_mlp called for the MLP kernel) beforehand;
+ * the call is asynchronous on stream. */
 hh_status hh_aca_block_apply_noalloc(hh_ctx *ctx, const double *Xt_dev, int32_t c, const double *Xs_dev, int32_t q,
                                      const double *F_dev, const hh_params *p, void *stream, double *y_dev,
                                      int32_t *rank_dev);
@@ -239,6 +256,17 @@ hh_status hh_export_blocks(const hh_blocks *blocks, int32_t *PG, int64_t *nG, in
  * block-local row / column indices, -1 past the rank) to host buffers. */
 hh_status hh_export_aca(const hh_hmat *h, int32_t *ranks, int32_t *piv_rows, int32_t *piv_cols, int64_t *nG,
                         int32_t *max_rank);
+
+/* Copies the stored ACA factors of Algorithm 2 to host buffers (Eq. 8: the
+ * admissible block (tau, sigma) is C Q, C = [c_0 .. c_{l-1}], Q = [q_0 ..
+ * q_{l-1}]).  fofs[nG + 1]: element offsets; block b's factors start at
+ * element fofs[b] and hold C as [l][9][c] then Q as [l][9][q] (the 3x3
+ * entries c_p(m)[u][v] at (p * 9 + 3u + v) * c + m, component-major), with l
+ * = ranks[b], c = |tau|, q = |sigma|.  factors receives n_factor * 9 reals of
+ * *real_bytes bytes each (8 for HH_FP64, else 4).  Pass NULL for fofs and
+ * factors to query n_factor and real_bytes.  HH_ERR_ARG if h was built with
+ * HH_FLAG_PIVOTS_ONLY.  Synchronises the device. */
+hh_status hh_export_factors(const hh_hmat *h, int64_t *fofs, void *factors, int64_t *n_factor, int32_t *real_bytes);
 
 typedef struct {
     double t_tree, t_part, t_near, t_aca, t_apply, t_acc; /* ms of the last call's stages (CUDA events) */

@@ -32,10 +32,10 @@ KERNELS = {"mlp": HH_MLP, "rpy": HH_RPY}
 EXPORTS = [
     "hh_default_params", "hh_create", "hh_destroy", "hh_last_error", "hh_set_mlp", "hh_build_tree",
     "hh_partition", "hh_aca", "hh_matvec", "hh_predict", "hh_matvec_backward", "hh_export_tree",
-    "hh_export_blocks", "hh_export_aca", "hh_stats", "hh_tree_free", "hh_blocks_free", "hh_hmat_free",
+    "hh_export_blocks", "hh_export_aca", "hh_export_factors", "hh_stats", "hh_tree_free", "hh_blocks_free", "hh_hmat_free",
     "hh_aca_block_apply_noalloc", "hh_eval_pairs", "hh_train_loss_grad", "hh_train_step",
     "hh_set_launch", "hh_get_launch", "hh_autotune", "hh_set_short_range", "hh_short_range",
-    "hh_filament_forces", "hh_filament_step",
+    "hh_filament_forces", "hh_filament_step", "hh_probe_throughput",
 ]
 
 
@@ -108,6 +108,8 @@ def lib():
             "hh_export_tree": (st, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
             "hh_export_blocks": (st, [_P, _P, _P, _P, _P]),
             "hh_export_aca": (st, [_P, _P, _P, _P, _P, _P]),
+            "hh_export_factors": (st, [_P, _P, _P, _P, _P]),
+            "hh_probe_throughput": (st, [_P, i32, ctypes.c_int64, _P, _P]),
             "hh_stats": (st, [_P, _P]),
             "hh_tree_free": (None, [_P]),
             "hh_blocks_free": (None, [_P]),
@@ -308,6 +310,15 @@ class Context:
                                       int(reps), _stream(stream), ctypes.byref(c)), "hh_autotune")
         return c.as_dict()
 
+    PROBES = {"mufu_ex2": 0, "mufu_rcp": 1, "mufu_tanh": 2, "ffma": 3, "dfma": 4, "silu": 5}
+
+    def probe(self, kind: str, iters: int = 1 << 16, stream=None) -> float:
+        """Operations per second of one arithmetic unit (see hh_probe_throughput)."""
+        v = ctypes.c_double()
+        self._check(lib().hh_probe_throughput(self._h, self.PROBES[kind], int(iters), _stream(stream),
+                                              ctypes.byref(v)), "hh_probe_throughput")
+        return v.value
+
     def stats(self) -> dict:
         s = CStats()
         self._check(lib().hh_stats(self._h, ctypes.byref(s)), "hh_stats")
@@ -420,6 +431,20 @@ class HMatrix(_Owned):
         self.ctx._check(lib().hh_export_aca(self._h, ranks.ctypes.data_as(_P), pI.ctypes.data_as(_P),
                                             pJ.ctypes.data_as(_P), None, None), "hh_export_aca")
         return ranks, pI, pJ
+
+    def export_factors(self):
+        """(fofs [nG + 1], factors [n_factor * 9]) as stored: block b holds C
+        [l][9][c] then Q [l][9][q] from element fofs[b] on."""
+        nG = ctypes.c_int64()
+        self.ctx._check(lib().hh_export_aca(self._h, None, None, None, ctypes.byref(nG), None), "hh_export_aca")
+        nf, rb = ctypes.c_int64(), ctypes.c_int32()
+        self.ctx._check(lib().hh_export_factors(self._h, None, None, ctypes.byref(nf), ctypes.byref(rb)),
+                        "hh_export_factors")
+        fofs = np.zeros(nG.value + 1, np.int64)
+        fac = np.zeros(9 * max(nf.value, 1), np.float64 if rb.value == 8 else np.float32)
+        self.ctx._check(lib().hh_export_factors(self._h, fofs.ctypes.data_as(_P), fac.ctypes.data_as(_P), None,
+                                                None), "hh_export_factors")
+        return fofs, fac[: 9 * nf.value]
 
 
 def _width_of(n_theta: int) -> int:

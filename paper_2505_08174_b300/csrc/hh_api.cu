@@ -706,6 +706,22 @@ hh_status hh_export_aca(const hh_hmat* h, int32_t* ranks, int32_t* piv_rows, int
     });
 }
 
+hh_status hh_export_factors(const hh_hmat* h, int64_t* fofs, void* factors, int64_t* n_factor, int32_t* real_bytes)
+{
+    if (!h) return HH_ERR_ARG;
+    return guarded(h->ctx, [&]() {
+        HH_REQUIRE(h->factors != nullptr, HH_ERR_ARG, "H-matrix built with HH_FLAG_PIVOTS_ONLY has no factors");
+        HH_CUDA(cudaDeviceSynchronize());
+        const int64_t n = h->blocks->nG;
+        if (fofs) HH_CUDA(cudaMemcpy(fofs, h->fofs, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
+        if (factors && h->n_factor > 0)
+            HH_CUDA(cudaMemcpy(factors, h->factors, (size_t)h->real_bytes * 9 * h->n_factor, cudaMemcpyDeviceToHost));
+        if (n_factor) *n_factor = h->n_factor;
+        if (real_bytes) *real_bytes = h->real_bytes;
+        return HH_OK;
+    });
+}
+
 hh_status hh_stats(hh_ctx* ctx, hh_stats_t* out)
 {
     if (!ctx || !out) return HH_ERR_ARG;

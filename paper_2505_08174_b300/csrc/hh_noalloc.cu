@@ -11,14 +11,14 @@
 // array of fixed size, so the call itself allocates nothing (it needs a
 // context set up earlier for the network weights and its status word).
 //
-// The array's host-side name is not a device address: its address is looked
-// up with cudaGetSymbolAddress once per device, on the first call made on
-// that device (so make the first call before any stream capture), and passed
-// to the kernels.  All calls share the array; each call rewrites everything
+// The array's host-side name is not a device address.  Every call looks the
+// address up with cudaGetSymbolAddress for the current device and passes it
+// to the kernels (nothing is cached, so a device reset or a new primary
+// context never leaves a stale address behind).  The first call on a device
+// may also load the library's device code there, so make it before any
+// stream capture.  All calls share the array; each call rewrites everything
 // it reads (the work counter included), but two calls that overlap on the
 // GPU -- on different streams, or from different threads -- race on it.
-#include <mutex>
-
 #include "hh_internal.h"
 
 namespace {
@@ -35,7 +35,8 @@ constexpr size_t NA_OFF_POS = NA_WS_BYTES;
 constexpr size_t NA_OFF_F = NA_OFF_POS + NA_POS_BYTES;
 constexpr size_t NA_OFF_PART = NA_OFF_F + NA_F_BYTES;
 constexpr size_t NA_OFF_META = NA_OFF_PART + NA_PART_BYTES;
-constexpr size_t NA_TOTAL = NA_OFF_META + NA_META_BYTES;   // 1,198,336 bytes
+constexpr size_t NA_TOTAL = NA_OFF_META + NA_META_BYTES;
+static_assert(NA_TOTAL == 1195264, "the header states the array's size (1.2 MB)");
 
 static __device__ __align__(256) unsigned char g_na_scratch[NA_TOTAL];
 
@@ -89,23 +90,18 @@ __global__ void k_na_out(const unsigned char* __restrict__ base, int c, double* 
     if (rank && threadIdx.x == 0) rank[0] = reinterpret_cast<const Meta*>(base + NA_OFF_META)->rank[0];
 }
 
-// Device address of g_na_scratch per device ordinal, looked up once.
-std::mutex g_na_mu;
-void* g_na_ptr[128] = {};
-
-void* na_scratch_for_current_device()
+// Device address of g_na_scratch on the current device, which must be the
+// context's device (the weights and the status word live there).
+void* na_scratch_for_device(int ctx_device)
 {
     int dev = -1;
     HH_CUDA(cudaGetDevice(&dev));
-    HH_REQUIRE(dev >= 0 && dev < 128, HH_ERR_ARG, "device ordinal out of range");
-    std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[dev]) {
-        void* p = nullptr;
-        HH_CUDA(cudaGetSymbolAddress(&p, g_na_scratch));
-        HH_REQUIRE(p != nullptr, HH_ERR_CUDA, "cudaGetSymbolAddress returned NULL");
-        g_na_ptr[dev] = p;
-    }
-    return g_na_ptr[dev];
+    HH_REQUIRE(dev == ctx_device, HH_ERR_ARG,
+               "hh_aca_block_apply_noalloc: the current device is not the context's device");
+    void* p = nullptr;
+    HH_CUDA(cudaGetSymbolAddress(&p, g_na_scratch));
+    HH_REQUIRE(p != nullptr, HH_ERR_CUDA, "cudaGetSymbolAddress returned NULL");
+    return p;
 }
 
 }  // namespace
@@ -122,8 +118,12 @@ extern "C" hh_status hh_aca_block_apply_noalloc(hh_ctx* ctx, const double* Xt_de
         HH_REQUIRE(c <= NA_MAX_SIDE && q <= NA_MAX_SIDE, HH_ERR_ARG,
                    "hh_aca_block_apply_noalloc: at most 128 targets and 128 sources per call");
         HH_REQUIRE(p->max_rank <= NA_MAX_RANK, HH_ERR_ARG, "max_rank must be <= 64");
+        HH_REQUIRE(p->precision != HH_BF16, HH_ERR_ARG,
+                   "hh_aca_block_apply_noalloc runs the SIMT kernels only: use HH_FP32 or HH_FP64");
         cudaStream_t s = (cudaStream_t)stream;
-        unsigned char* base = static_cast<unsigned char*>(na_scratch_for_current_device());
+        unsigned char* base = static_cast<unsigned char*>(na_scratch_for_device(ctx->device));
+        // the status bits of this call start from zero (a memset allocates nothing)
+        HH_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), s));
         Meta* meta = reinterpret_cast<Meta*>(base + NA_OFF_META);
         k_na_stage<<<1, 256, 0, s>>>(Xt_dev, c, Xs_dev, q, F_dev, base);
         HH_CHECK_LAUNCH();

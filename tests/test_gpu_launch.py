@@ -76,3 +76,17 @@ def test_autotune_picks_a_candidate_and_keeps_it(ctx):
     c2 = hh.Context()
     c2.set_mlp(THETA, 32)
     assert oracle.rel_error(c2.predict(X, F, p).cpu().numpy(), U) < 2e-5
+
+
+def test_unit_probes_are_physical(ctx):
+    # hh_probe_throughput: each unit's rate is positive and below what 148 SMs
+    # could issue at 2.1 GHz (128 FP32 lanes per SM per clock; MUFU and FP64
+    # far fewer), and the SiLU (two MUFU operations) is slower than one MUFU op
+    r = {k: ctx.probe(k, 1 << 12) for k in ctx.PROBES}
+    lanes_ops = 148 * 128 * 2.1e9
+    for k, v in r.items():
+        assert 0 < v < lanes_ops, (k, v)
+    assert r["silu"] < r["mufu_ex2"]
+    assert r["dfma"] < r["ffma"]
+    with pytest.raises(hh.HHError):
+        ctx.probe("ffma", 0)

@@ -347,6 +347,98 @@ def test_aca_rank_grows_as_eps_falls():
 
 
 # --------------------------------------------------------------------------
+# ACA pivot guard (Algorithm 2 with the determinant fallback) and the
+# randomised j_1 of Algorithm 2 (rule 1)
+# --------------------------------------------------------------------------
+def _fallback_block(P00, col1):
+    """3 x 2 block whose first column (j_1 = 0) is given element by element."""
+    rng = np.random.default_rng(11)
+    G = np.zeros((3, 2, 3, 3))
+    for m in range(3):
+        G[m, 0] = P00[m]
+        G[m, 1] = col1[m] if col1 is not None else rng.normal(size=(3, 3))
+    return G
+
+
+def test_aca_fallback_takes_largest_det():
+    # column 0: row 0 has the largest Frobenius norm (10) but is singular;
+    # row 1 is second by norm (|.|_F ~ 3.00, det 0.03); row 2 has the largest
+    # |det| (3.375).  The guard must take row 2 -- not the smallest |det|
+    # (row 0) and not the next row by norm (row 1).
+    P = [np.diag([10.0, 0.0, 0.0]), np.diag([3.0, 0.1, 0.1]), 1.5 * np.eye(3)]
+    G = _fallback_block(P, None)
+    res = oracle.aca_dense(G, eps=1e-4, max_rank=8)
+    assert res["I"][0] == 2 and res["J"][0] == 0
+    assert np.allclose(res["C"][0, 2], np.eye(3), atol=1e-15)      # c_0 scaled by its pivot's inverse
+    # two column steps reach k = min(c, q): the 9 x 6 scalar matrix is reproduced
+    D = _dense_block(G)
+    assert np.linalg.norm(_dense_block(G - _cq(res))) <= 10 * 1e-4 * np.linalg.norm(D)
+
+
+def test_aca_fallback_on_ill_conditioned_pivot():
+    # row 0 is the Frobenius-best and non-singular (det 1e-8) but its
+    # reciprocal condition number 1/(|P|_F |P^-1|_F) ~ 7e-12 is below 1e-10:
+    # the guard replaces it by the eligible row of largest |det| (row 2, det 3.375)
+    P = [np.diag([10.0, 10.0, 1e-10]), np.diag([3.0, 0.1, 0.1]), 1.5 * np.eye(3)]
+    res = oracle.aca_dense(_fallback_block(P, None), eps=1e-4, max_rank=8)
+    assert res["I"][0] == 2
+    # just above the threshold (rc ~ 7e-10) the Frobenius-best row is kept
+    P[0] = np.diag([10.0, 10.0, 1e-8])
+    res = oracle.aca_dense(_fallback_block(P, None), eps=1e-4, max_rank=8)
+    assert res["I"][0] == 0
+
+
+def test_aca_fallback_without_usable_pivot_stops():
+    # every element of the first column is singular: no eligible row has
+    # |det| > 0, so the block ends with the pairs found so far (none)
+    P = [np.diag([10.0, 0.0, 0.0]), np.diag([0.0, 3.0, 0.0]), np.diag([0.0, 0.0, 1.0])]
+    res = oracle.aca_dense(_fallback_block(P, None), eps=1e-4, max_rank=8)
+    assert res["rank"] == 0
+
+
+def test_aca_fallback_skips_used_rows():
+    # Step 0 takes row 0 (the only non-zero row of column 0); its scaled
+    # element C_0(0) = P P^-1 is the identity up to rounding.  At step 1 the
+    # column residual of the used row 0 is that rounding noise (tiny but of
+    # full rank), while the unused rows 1..3 are exactly singular: the guard
+    # finds no eligible pivot and stops at rank 1.  A guard that forgot the
+    # used-row test would take row 0 a second time.
+    rng = np.random.default_rng(3)
+    G = np.zeros((4, 3, 3, 3))
+    G[0, 0] = 10.0 * rng.normal(size=(3, 3))
+    G[0, 1] = 5.0 * rng.normal(size=(3, 3))
+    G[0, 2] = 0.1 * rng.normal(size=(3, 3))
+    for m, a in zip((1, 2, 3), (3.0, 2.0, 1.0)):
+        G[m, 1] = np.diag([a, 0.0, 0.0])
+    res = oracle.aca_dense(G, eps=1e-6, max_rank=8)
+    assert res["rank"] == 1 and res["I"][0] == 0 and res["J"][0] == 0
+
+
+_SPLITMIX64_SEED0 = (0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC)
+
+
+def test_j1_rule1_is_splitmix64():
+    # Rule 1 draws j_1 = splitmix64(seed ^ (tau << 32) ^ sigma) mod q.  The
+    # published SplitMix64 stream started from state 0 gives outputs
+    # mix(n * gamma), n = 1, 2, ...; with tau = sigma = 0 and seed = (n-1) gamma
+    # the oracle must return output n mod q.  Four moduli whose product
+    # exceeds 2^64 pin every bit of each output.
+    gamma, mask = 0x9E3779B97F4A7C15, (1 << 64) - 1
+    for n, out in enumerate(_SPLITMIX64_SEED0):
+        seed = (n * gamma) & mask
+        for q in (2 ** 31 - 1, 1000003, 65536, 97):
+            assert oracle.j1(1, seed, 0, 0, q) == out % q
+    # tau enters shifted by 32 bits and sigma unshifted, both xor-ed into the seed
+    t, s = 5, 7
+    seed = gamma ^ (t << 32) ^ s
+    assert oracle.j1(1, seed, t, s, 1000003) == _SPLITMIX64_SEED0[1] % 1000003
+    assert oracle.j1(1, seed, s, t, 1000003) != _SPLITMIX64_SEED0[1] % 1000003
+    # rule 0 and one-column blocks give the first source
+    assert oracle.j1(0, seed, t, s, 1000003) == 0
+    assert oracle.j1(1, seed, t, s, 1) == 0
+
+
+# --------------------------------------------------------------------------
 # H-matrix product
 # --------------------------------------------------------------------------
 def test_hmatvec_exact_when_nothing_far():
