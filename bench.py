@@ -234,7 +234,8 @@ def run_ours(args, rank, world):
     ctx = hh.Context(dev)
     ctx.set_mlp(theta, 32)
     prec = args.precision
-    p = hh.Params(leaf_size=args.leaf, eta=1.0, eps=args.eps, max_rank=48, precision=prec)
+    p = hh.Params(leaf_size=args.leaf, eta=1.0, eps=args.eps, max_rank=48, precision=prec,
+                  mem_budget=args.budget_mb << 20)
     Xd = torch.as_tensor(X).cuda()
     Fd = torch.as_tensor(F).cuda()
     U = torch.empty_like(Xd)
@@ -267,6 +268,17 @@ def run_ours(args, rank, world):
     value, total_ms = weak_scaling_value(n, args.steps, float(np.sum(step_ms)), dist, "cuda")
     clocks = clk.summary()
     st = ctx.stats()
+    if args.profile:   # the timed predictions only (profiling runs): no accuracy, baseline or e2e legs
+        if rank == 0:
+            print(json.dumps({"profile": True, "n": n, "ms_per_step": total_ms / args.steps, "value": value,
+                              "stages_ms": {k: st[k] for k in ("t_tree", "t_part", "t_near", "t_aca", "t_acc")},
+                              "n_aca_queries": st["n_aca_queries"], "n_near_pairs": st["n_near_pairs"],
+                              "n_aca_rounds": st["n_aca_rounds"], "t_aca_tiles": st["t_aca_tiles"],
+                              "t_aca_steps": st["t_aca_steps"], "launches": launches, "clocks": clocks}),
+                  flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
 
     # end to end: pinned host inputs, H2D + predict + D2H per step
     Xh = torch.as_tensor(X).pin_memory()
@@ -582,6 +594,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-rows", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--budget-mb", type=int, default=0,
+                    help="memory budget of the BF16 ACA's active blocks in MB (0 = the library default)")
+    ap.add_argument("--profile", action="store_true",
+                    help="run the warm-up and timed predictions only and print their stage times (for ncu runs)")
     ap.add_argument("--clocks-csv", default=None,
                     help="keep the raw nvidia-smi clock samples of the timed region in this file")
     ap.add_argument("--workload", default="cube1m",

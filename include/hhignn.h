@@ -98,10 +98,13 @@ typedef struct {
     int32_t shard_id;    /* this shard's share of the block work lists                      */
     int32_t n_shards;    /* number of shards (1 = everything)                               */
     int32_t flags;       /* HH_FLAG_* bits, 0 = none                                        */
+    int64_t mem_budget;  /* bytes the BF16 block ACA may hold for its active blocks' factor
+                            workspaces (the query groups of Section 3.3); 0 = 8 GB         */
 } hh_params;
 
 /* Fills *p with the defaults: leaf 32, eta 1, eps 1e-4, max_rank 48, FP32,
- * MLP, a = mu = 1, j1_rule 0, seed 0, one shard, no flags. */
+ * MLP, a = mu = 1, j1_rule 0, seed 0, one shard, no flags, default ACA
+ * memory budget. */
 void hh_default_params(hh_params *p);
 
 /* Context: owns the MLP weights copy, a device status word and counters.
@@ -285,6 +288,10 @@ typedef struct {
                                ordered temporaries (plus any other user of
                                that pool); -1 if the driver does not report
                                it                                            */
+    int64_t n_aca_rounds;   /* rounds of the BF16 block ACA (0 for the other
+                               precisions)                                   */
+    double t_aca_tiles;     /* ms in the BF16 ACA's tile kernels (CUDA events) */
+    double t_aca_steps;     /* ms in its step kernels (CUDA events)            */
 } hh_stats_t;
 
 /* Short-range networks of Eq. 6 (Eq. 2 with the Eq. 4 normalisations; the
@@ -326,6 +333,11 @@ hh_status hh_stats(hh_ctx *ctx, hh_stats_t *out);
  *                  tensor-core kernel)
  *   near_cps       CTAs per SM of the tensor-core near-field kernel, 1..8,
  *                  default 4
+ *   rounds_min_cq  (HH_BF16) admissible blocks with c + q above this value go
+ *                  through the round-based ACA (every block of a size class
+ *                  advancing one phase per round, its rows spread over the
+ *                  whole GPU) instead of one CTA team each; 513..2^30, or 0
+ *                  for the default 4096
  * Grids are further capped by the amount of work and the workspace budget;
  * the SM's occupancy limits how many CTAs actually run at once. */
 typedef struct {
@@ -333,7 +345,8 @@ typedef struct {
     int32_t aca_small_cps;
     int32_t aca_large_cps;
     int32_t near_cps;
-    int32_t reserved[4];   /* 0 */
+    int32_t rounds_min_cq;
+    int32_t reserved[3];   /* 0 */
 } hh_launch_cfg;
 
 /* Set / read ctx's launch shape (as stored: 0 = default).  Out-of-range
@@ -346,7 +359,8 @@ hh_status hh_get_launch(hh_ctx *ctx, hh_launch_cfg *cfg);
  * shapes and keeps the fastest on ctx (also written to *best when not NULL).
  * Coordinate descent from ctx's current shape: each field in turn is swept
  * over a fixed candidate list (small_max 128 / 256 / 512, aca_small_cps 1..4,
- * aca_large_cps 1 / 2 / 4, near_cps 2 / 4 / 8) with the others held, and the
+ * aca_large_cps 1 / 2 / 4, near_cps 2 / 4 / 8, rounds_min_cq 2048 / 4096 /
+ * 16384) with the others held, and the
  * value of the smallest median time over reps (>= 1) predictions is kept.
  * Results do not depend on the launch shape beyond FP rounding order of the
  * per-block partial sums (none: each block's output is written once). */

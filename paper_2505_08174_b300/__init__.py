@@ -50,7 +50,7 @@ class CParams(ctypes.Structure):
                 ("max_rank", ctypes.c_int32), ("precision", ctypes.c_int32), ("kernel", ctypes.c_int32),
                 ("radius", ctypes.c_double), ("viscosity", ctypes.c_double), ("j1_rule", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("shard_id", ctypes.c_int32), ("n_shards", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("mem_budget", ctypes.c_int64)]
 
 
 class CStats(ctypes.Structure):
@@ -60,12 +60,14 @@ class CStats(ctypes.Structure):
                 ("n_blocks_G", ctypes.c_int64), ("n_blocks_H", ctypes.c_int64), ("n_nodes", ctypes.c_int64),
                 ("rank_hist", ctypes.c_int64 * 65), ("t_kernel_aca", ctypes.c_double),
                 ("t_kernel_near", ctypes.c_double), ("n_launches", ctypes.c_int64), ("t_short", ctypes.c_double),
-                ("n_short_pairs", ctypes.c_int64), ("mem_peak_bytes", ctypes.c_int64)]
+                ("n_short_pairs", ctypes.c_int64), ("mem_peak_bytes", ctypes.c_int64),
+                ("n_aca_rounds", ctypes.c_int64), ("t_aca_tiles", ctypes.c_double), ("t_aca_steps", ctypes.c_double)]
 
 
 class CLaunch(ctypes.Structure):
     _fields_ = [("small_max", ctypes.c_int32), ("aca_small_cps", ctypes.c_int32),
-                ("aca_large_cps", ctypes.c_int32), ("near_cps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("aca_large_cps", ctypes.c_int32), ("near_cps", ctypes.c_int32), ("rounds_min_cq", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -141,7 +143,7 @@ FLAG_PIVOTS_ONLY = 2
 
 def Params(leaf_size=32, eta=1.0, eps=1e-4, max_rank=48, precision="fp32", kernel="mlp", radius=1.0,
            viscosity=1.0, j1_rule=0, seed=0, shard_id=0, n_shards=1, short_range=False,
-           pivots_only=False) -> CParams:
+           pivots_only=False, mem_budget=0) -> CParams:
     p = CParams()
     lib().hh_default_params(ctypes.byref(p))
     p.leaf_size, p.eta, p.eps, p.max_rank = leaf_size, eta, eps, max_rank
@@ -150,6 +152,7 @@ def Params(leaf_size=32, eta=1.0, eps=1e-4, max_rank=48, precision="fp32", kerne
     p.radius, p.viscosity, p.j1_rule, p.seed = radius, viscosity, j1_rule, seed
     p.shard_id, p.n_shards = shard_id, n_shards
     p.flags = (FLAG_SHORT_RANGE if short_range else 0) | (FLAG_PIVOTS_ONLY if pivots_only else 0)
+    p.mem_budget = int(mem_budget)
     return p
 
 
@@ -292,8 +295,8 @@ class Context:
         return F, U
 
     # -- launch shape and autotuner ---------------------------------------------
-    def set_launch(self, small_max=0, aca_small_cps=0, aca_large_cps=0, near_cps=0):
-        c = CLaunch(small_max, aca_small_cps, aca_large_cps, near_cps)
+    def set_launch(self, small_max=0, aca_small_cps=0, aca_large_cps=0, near_cps=0, rounds_min_cq=0):
+        c = CLaunch(small_max, aca_small_cps, aca_large_cps, near_cps, rounds_min_cq)
         self._check(lib().hh_set_launch(self._h, ctypes.byref(c)), "hh_set_launch")
 
     def get_launch(self) -> dict:

@@ -504,6 +504,28 @@ __global__ void __launch_bounds__(128) k_apply(const R* __restrict__ fac, const 
     }
 }
 
+// Size classes of the BF16 rounds: c + q in (2^e, 2^(e+1)], largest first;
+// pos[i] = first item of the sorted list with c + q <= 2^(RC_TOP - i).
+constexpr int RC_TOP = 30, RC_N = RC_TOP - 7 + 1;   // the last class is c + q <= 128
+
+__global__ void k_round_classes(const uint64_t* __restrict__ key, int64_t n, int64_t* __restrict__ pos,
+                                int32_t* __restrict__ mx, int32_t min_cq)
+{
+    const int i = threadIdx.x;
+    auto cq = [&](int64_t x) { return (int32_t)(0x7fffffffu - (uint32_t)(key[x] >> 32)); };
+    if (i <= RC_N) {   // pos[RC_N]: the items with c + q > min_cq
+        const int32_t lim = i < RC_N ? 1 << (RC_TOP - i) : min_cq;
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (cq(mid) <= lim) hi = mid; else lo = mid + 1;
+        }
+        pos[i] = lo;
+        if (i < RC_N) mx[i + 1] = lo < n ? cq(lo) : 0;   // largest c + q of the class starting at lo
+    }
+    if (i == 0) mx[0] = n > 0 ? cq(0) : 0;
+}
+
 template <typename R>
 void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_params& p, const AcaRun& r,
                cudaStream_t s)
@@ -536,6 +558,10 @@ void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_para
     k_compact<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(fs, os, nG, ws);
     HH_CHECK_LAUNCH();
     std::vector<AcaClass> cls;   // size classes of the large list
+    // the round engine's classes of the large list (BF16): c + q in (2^e, 2^(e+1)]
+    std::vector<int64_t> rb;
+    int32_t rm[RC_N + 1] = {};
+    int64_t n_rounds = 0;
     if (h[1] > 0) {
         uint64_t* lk = dev_alloc_t<uint64_t>(h[1], s);
         k_compact_keys<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(fl, ol, key, nG, lk);
@@ -552,10 +578,29 @@ void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_para
         HH_CUDA(cudaMemcpyAsync(hp, cpos, sizeof hp, cudaMemcpyDeviceToHost, s));
         HH_CUDA(cudaMemcpyAsync(hm, cmx, sizeof hm, cudaMemcpyDeviceToHost, s));
         HH_CUDA(cudaStreamSynchronize(s));
-        int64_t b0 = 0;
+        if (use_tc) {
+            // the prefix of blocks with c + q > rounds_min_cq goes to the round engine
+            int64_t* rpos = dev_alloc_t<int64_t>(RC_N + 1, s);
+            int32_t* rmx = dev_alloc_t<int32_t>(RC_N + 1, s);
+            k_round_classes<<<1, 32, 0, s>>>(lk, h[1], rpos, rmx, lc.rounds_min_cq);
+            HH_CHECK_LAUNCH();
+            int64_t hp2[RC_N + 1];
+            HH_CUDA(cudaMemcpyAsync(hp2, rpos, sizeof hp2, cudaMemcpyDeviceToHost, s));
+            HH_CUDA(cudaMemcpyAsync(rm, rmx, sizeof rm, cudaMemcpyDeviceToHost, s));
+            HH_CUDA(cudaStreamSynchronize(s));
+            n_rounds = hp2[RC_N];
+            rb.assign(RC_N + 2, 0);
+            for (int i = 0; i < RC_N; ++i) rb[i + 1] = std::min(hp2[i], n_rounds);
+            rb[RC_N + 1] = n_rounds;
+            dev_free(rpos, s);
+            dev_free(rmx, s);
+        }
+        int64_t b0 = n_rounds;
         for (int i = 0; i <= N_CLASS_LIMITS; ++i) {
             const int64_t e = i < N_CLASS_LIMITS ? hp[i] : h[1];
-            if (e > b0) cls.push_back(AcaClass{b0, e, hm[i == 0 ? 0 : i]});
+            if (e > b0) cls.push_back(AcaClass{b0, e, std::min(hm[i == 0 ? 0 : i], b0 == n_rounds && n_rounds > 0
+                                                                                        ? (int32_t)lc.rounds_min_cq
+                                                                                        : hm[i == 0 ? 0 : i])});
             b0 = std::max(b0, e);
         }
         dev_free(cpos, s);
@@ -577,7 +622,8 @@ void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_para
     const int kind = kernel_kind(p, ctx->width);
     if constexpr (sizeof(R) == 4) {
         if (use_tc) {
-            aca_tc_run(ctx, t, bl, p, r, ws, h[0], wl, cls.data(), (int)cls.size(), max_small_cq, s);
+            aca_tc_run(ctx, t, bl, p, r, ws, h[0], wl, cls.data(), (int)cls.size(), wl,
+                       n_rounds > 0 ? rb.data() : nullptr, rm, n_rounds > 0 ? RC_N + 1 : 0, max_small_cq, s);
             dev_free(fs, s); dev_free(fl, s); dev_free(os, s); dev_free(ol, s); dev_free(key, s); dev_free(tot, s);
             dev_free(ws, s); dev_free(wl, s);
             return;

@@ -397,28 +397,29 @@ void launch_tc(hh_ctx* ctx, const AcaArgs<float>& A, int64_t grid, int mode, cud
 
 }  // namespace
 
-// Tensor-core ACA over the classified work lists (same contract as the SIMT
-// launches in hh_aca.cu): large blocks (c or q > 512, by decreasing size)
-// on CTA teams, then small blocks on warp teams.
+// Tensor-core ACA over the classified work lists, on three streams at once:
+// small blocks on warp teams (caller's stream), mid-size blocks on CTA teams
+// by size class (second stream), and the largest blocks through the round
+// engine of hh_aca_rounds.cu (third stream; its host loop runs last, so the
+// other two lists are already queued).  Both extra streams are forked from
+// and joined back to the caller's stream by events.
 void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_params& p, const AcaRun& r,
                 const int32_t* work_small, int64_t n_small, const int32_t* work_large, const AcaClass* cls,
-                int n_cls, int max_small_cq, cudaStream_t s)
+                int n_cls, const int32_t* work_rounds, const int64_t* rcls_begin, const int32_t* rcls_max_cq,
+                int n_rcls, int max_small_cq, cudaStream_t s)
 {
     HH_REQUIRE(p.kernel == HH_MLP && p.precision == HH_BF16, HH_ERR_ARG, "tensor-core ACA needs the BF16 MLP kernel");
     const int mr = std::min(p.max_rank, MAXR);
     const hh_launch_cfg lc = resolved_launch(ctx, true);
     AcaArgs<float> A = make_aca_args<float>(ctx, t, bl, p, r);
-    // the CTA-team size classes run on the context's second stream, beside
-    // the warp teams: the serial tails of the few largest blocks overlap with
-    // the bulk of the small blocks
-    const bool both = n_cls > 0 && n_small > 0;
-    cudaStream_t sl = both ? ctx->aux : s;
+    const int64_t n_rounds = n_rcls > 0 ? rcls_begin[n_rcls] : 0;
     HH_CUDA(cudaEventRecord(ctx->kev[2], s));
-    if (both) {
-        HH_CUDA(cudaEventRecord(ctx->fork_ev, s));
-        HH_CUDA(cudaStreamWaitEvent(sl, ctx->fork_ev, 0));
-    }
-    // joins the second stream back even when an error unwinds from here, so
+    HH_CUDA(cudaEventRecord(ctx->fork_ev, s));
+    const cudaStream_t sl = n_cls > 0 ? ctx->aux : s;
+    const cudaStream_t sr = n_rounds > 0 ? ctx->aux2 : s;
+    if (n_cls > 0) HH_CUDA(cudaStreamWaitEvent(sl, ctx->fork_ev, 0));
+    if (n_rounds > 0) HH_CUDA(cudaStreamWaitEvent(sr, ctx->fork_ev, 0));
+    // joins the extra streams back even when an error unwinds from here, so
     // the caller's stream-ordered frees never overtake a launch still in flight
     struct Join {
         cudaStream_t from, into;
@@ -426,6 +427,7 @@ void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_par
         bool on;
         void now()
         {
+            if (!on) return;
             on = false;
             HH_CUDA(cudaEventRecord(ev, from));
             HH_CUDA(cudaStreamWaitEvent(into, ev, 0));
@@ -434,27 +436,7 @@ void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_par
         {
             if (on && cudaEventRecord(ev, from) == cudaSuccess) (void)cudaStreamWaitEvent(into, ev, 0);
         }
-    } join{sl, s, ctx->join_ev, both};
-    if (n_cls > 0) {
-        for (int i = 0; i < n_cls; ++i) {
-            const AcaClass& k = cls[i];
-            int64_t stride = (int64_t)k.max_cq * 9 * mr + ceil_div(k.max_cq, (int64_t)sizeof(float));
-            stride = ceil_div(stride * (int64_t)sizeof(float), 256) * 256 / (int64_t)sizeof(float);
-            const int64_t budget = aca_workspace_budget();
-            int64_t teams = std::min<int64_t>(k.end - k.begin, (int64_t)lc.aca_large_cps * ctx->n_sm);
-            teams = std::max<int64_t>(1, std::min<int64_t>(teams, budget / (stride * (int64_t)sizeof(float))));
-            float* scratch = dev_alloc_t<float>(stride * teams, sl);
-            HH_CUDA(cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), sl));
-            AcaArgs<float> B = A;
-            B.work = work_large + k.begin;
-            B.n_work = k.end - k.begin;
-            B.scratch = scratch;
-            B.team_stride = stride;
-            if (ctx->width == 32) launch_tc<32, CtaTeamT<TC_T>>(ctx, B, teams, r.mode, sl);
-            else launch_tc<64, CtaTeamT<TC_T>>(ctx, B, teams, r.mode, sl);
-            dev_free(scratch, sl);
-        }
-    }
+    } join_l{sl, s, ctx->join_ev, n_cls > 0}, join_r{sr, s, ctx->join2_ev, n_rounds > 0};
     if (n_small > 0) {
         constexpr int NT = TC_T / 32;
         const int64_t blocks = std::min<int64_t>(ceil_div(n_small, NT), (int64_t)lc.aca_small_cps * ctx->n_sm);
@@ -472,7 +454,29 @@ void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_par
         else launch_tc<64, WarpTeam>(ctx, B, blocks, r.mode, s);
         dev_free(scratch, s);
     }
-    if (both) join.now();
+    for (int i = 0; i < n_cls; ++i) {
+        const AcaClass& k = cls[i];
+        int64_t stride = (int64_t)k.max_cq * 9 * mr + ceil_div(k.max_cq, (int64_t)sizeof(float));
+        stride = ceil_div(stride * (int64_t)sizeof(float), 256) * 256 / (int64_t)sizeof(float);
+        const int64_t budget = aca_budget_bytes(p);
+        int64_t teams = std::min<int64_t>(k.end - k.begin, (int64_t)lc.aca_large_cps * ctx->n_sm);
+        teams = std::max<int64_t>(1, std::min<int64_t>(teams, budget / (stride * (int64_t)sizeof(float))));
+        float* scratch = dev_alloc_t<float>(stride * teams, sl);
+        HH_CUDA(cudaMemsetAsync(A.counter, 0, sizeof(unsigned long long), sl));
+        AcaArgs<float> B = A;
+        B.work = work_large + k.begin;
+        B.n_work = k.end - k.begin;
+        B.scratch = scratch;
+        B.team_stride = stride;
+        if (ctx->width == 32) launch_tc<32, CtaTeamT<TC_T>>(ctx, B, teams, r.mode, sl);
+        else launch_tc<64, CtaTeamT<TC_T>>(ctx, B, teams, r.mode, sl);
+        dev_free(scratch, sl);
+    }
+    ctx->stats.n_aca_rounds = 0;
+    ctx->stats.t_aca_tiles = ctx->stats.t_aca_steps = 0.0;
+    if (n_rounds > 0) aca_rounds_run(ctx, t, bl, p, r, work_rounds, rcls_begin, rcls_max_cq, n_rcls, sr, false);
+    join_l.now();
+    join_r.now();
     HH_CUDA(cudaEventRecord(ctx->kev[3], s));
     ctx->kev_aca_used |= 2;
 }

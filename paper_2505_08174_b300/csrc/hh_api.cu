@@ -64,6 +64,7 @@ void check_params(const hh_ctx* ctx, const hh_params* p)
     HH_REQUIRE(p->n_shards >= 1 && p->shard_id >= 0 && p->shard_id < p->n_shards, HH_ERR_ARG, "bad shard");
     HH_REQUIRE(p->j1_rule == 0 || p->j1_rule == 1, HH_ERR_ARG, "j1_rule must be 0 or 1");
     HH_REQUIRE((p->flags & ~(HH_FLAG_SHORT_RANGE | HH_FLAG_PIVOTS_ONLY)) == 0, HH_ERR_ARG, "unknown flags");
+    HH_REQUIRE(p->mem_budget >= 0, HH_ERR_ARG, "mem_budget must be >= 0 (0 = default)");
     HH_REQUIRE(!(p->flags & HH_FLAG_SHORT_RANGE) || ctx->sr_width > 0, HH_ERR_ARG,
                "HH_FLAG_SHORT_RANGE needs hh_set_short_range");
 }
@@ -235,9 +236,13 @@ hh_status hh_create(hh_ctx** out, int device)
         HH_CUDA(cudaMemset(ctx->d_counters, 0, 8 * sizeof(unsigned long long)));
         for (auto& e : ctx->ev) HH_CUDA(cudaEventCreate(&e));
         HH_CUDA(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+        HH_CUDA(cudaStreamCreateWithFlags(&ctx->aux2, cudaStreamNonBlocking));
+        HH_CUDA(cudaEventCreateWithFlags(&ctx->join2_ev, cudaEventDisableTiming));
         HH_CUDA(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming));
         HH_CUDA(cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming));
         for (auto& e : ctx->kev) HH_CUDA(cudaEventCreate(&e));
+        HH_CUDA(cudaEventCreateWithFlags(&ctx->poll_ev, cudaEventDisableTiming));
+        HH_CUDA(cudaMallocHost(&ctx->h_pinned, sizeof(int) * 4));
         return HH_OK;
     });
     cudaSetDevice(prev);
@@ -267,8 +272,12 @@ void hh_destroy(hh_ctx* ctx)
     if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
     if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
     if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->aux2) cudaStreamDestroy(ctx->aux2);
+    if (ctx->join2_ev) cudaEventDestroy(ctx->join2_ev);
     for (auto& e : ctx->kev)
         if (e) cudaEventDestroy(e);
+    if (ctx->poll_ev) cudaEventDestroy(ctx->poll_ev);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     delete ctx;
 }
 
@@ -799,7 +808,9 @@ hh_status hh_set_launch(hh_ctx* ctx, const hh_launch_cfg* cfg)
         auto ok = [](int32_t v) { return v >= 0 && v <= 8; };
         HH_REQUIRE(ok(cfg->aca_small_cps) && ok(cfg->aca_large_cps) && ok(cfg->near_cps), HH_ERR_ARG,
                    "CTAs per SM must be 0 or in [1, 8]");
-        for (int i = 0; i < 4; ++i) HH_REQUIRE(cfg->reserved[i] == 0, HH_ERR_ARG, "reserved fields must be 0");
+        HH_REQUIRE(cfg->rounds_min_cq == 0 || (cfg->rounds_min_cq >= 513 && cfg->rounds_min_cq <= (1 << 30)),
+                   HH_ERR_ARG, "rounds_min_cq must be 0 or in [513, 2^30]");
+        for (int i = 0; i < 3; ++i) HH_REQUIRE(cfg->reserved[i] == 0, HH_ERR_ARG, "reserved fields must be 0");
         ctx->launch = *cfg;
         return HH_OK;
     });
@@ -857,11 +868,13 @@ hh_status hh_autotune(hh_ctx* ctx, const double* X_dev, const int64_t* offsets, 
     static const int32_t cand_small_cps[] = {1, 2, 3, 4};
     static const int32_t cand_large_cps[] = {1, 2, 4};
     static const int32_t cand_near_cps[] = {2, 4, 8};
+    static const int32_t cand_rounds[] = {2048, 4096, 16384};
     struct Field { int32_t hh_launch_cfg::*f; const int32_t* v; int nv; };
     const Field fields[] = {{&hh_launch_cfg::small_max, cand_small_max, 3},
                             {&hh_launch_cfg::aca_small_cps, cand_small_cps, 4},
                             {&hh_launch_cfg::aca_large_cps, cand_large_cps, 3},
-                            {&hh_launch_cfg::near_cps, cand_near_cps, 3}};
+                            {&hh_launch_cfg::near_cps, cand_near_cps, 3},
+                            {&hh_launch_cfg::rounds_min_cq, cand_rounds, 3}};
     for (const Field& fd : fields) {
         for (int i = 0; i < fd.nv && st == HH_OK; ++i) {
             hh_launch_cfg c = cur;

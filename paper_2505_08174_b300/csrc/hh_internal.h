@@ -32,6 +32,10 @@ struct hh_ctx {
     hh_launch_cfg launch{};              // 0 fields: defaults (see resolved_launch)
     cudaStream_t aux = nullptr;          // second stream: CTA-team ACA classes beside the warp teams
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    cudaStream_t aux2 = nullptr;         // third stream: the round-based ACA of the largest blocks
+    cudaEvent_t join2_ev = nullptr;
+    cudaEvent_t poll_ev = nullptr;       // the ACA rounds' progress reads
+    int* h_pinned = nullptr;             // pinned host word those reads land in
     // short-range networks (hh_set_short_range): FP32 and FP64 copies
     float* sr_theta_s32 = nullptr;
     float* sr_theta_332 = nullptr;
@@ -50,6 +54,7 @@ inline hh_launch_cfg resolved_launch(const hh_ctx* ctx, bool tc)
     if (c.aca_small_cps <= 0) c.aca_small_cps = 4;
     if (c.aca_large_cps <= 0) c.aca_large_cps = tc ? 4 : 2;
     if (c.near_cps <= 0) c.near_cps = 4;
+    if (c.rounds_min_cq <= 0) c.rounds_min_cq = 4096;
     return c;
 }
 
@@ -166,11 +171,32 @@ inline int64_t aca_workspace_budget()
     return std::max<int64_t>((int64_t)4 << 30, (int64_t)(fr / 2));
 }
 
-// Tensor-core ACA (hh_aca_tc.cu, precision HH_BF16 with the MLP kernel) over
-// the small (warp-team) and large (CTA-team) work lists built by aca_run.
+// Bytes the BF16 block ACA may hold for its active blocks (hh_params.mem_budget,
+// default 8 GB).
+inline int64_t aca_budget_bytes(const hh_params& p) { return p.mem_budget > 0 ? p.mem_budget : (int64_t)8 << 30; }
+
+inline int* ctx_pinned_int(hh_ctx* ctx) { return ctx->h_pinned; }
+
+// Round-based tensor-core ACA (hh_aca_rounds.cu, precision HH_BF16): the
+// admissible blocks of this shard sorted by decreasing c + q (work_sorted),
+// cut into size classes [cls_begin[i], cls_begin[i+1]) whose largest block
+// has c + q = cls_max_cq[i].
+// own_events: record the ACA kernel events (kev[2], kev[3]) around the run.
+void aca_rounds_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_params& p, const AcaRun& r,
+                    const int32_t* work_sorted, const int64_t* cls_begin, const int32_t* cls_max_cq, int n_cls,
+                    cudaStream_t s, bool own_events);
+
+// Tensor-core ACA (hh_aca_tc.cu, precision HH_BF16 with the MLP kernel),
+// three lists run concurrently: the small blocks (c, q <= small_max) on warp
+// teams on stream s; the mid-size blocks (work_large, size classes cls) on
+// CTA teams on the context's second stream; the largest blocks (c + q above
+// rounds_min_cq; work_rounds, sorted by decreasing c + q, in the size classes
+// rcls_begin / rcls_max_cq of aca_rounds_run) through the round engine on the
+// third stream.
 void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_params& p, const AcaRun& r,
                 const int32_t* work_small, int64_t n_small, const int32_t* work_large, const AcaClass* cls,
-                int n_cls, int max_small_cq, cudaStream_t s);
+                int n_cls, const int32_t* work_rounds, const int64_t* rcls_begin, const int32_t* rcls_max_cq,
+                int n_rcls, int max_small_cq, cudaStream_t s);
 
 // Tensor-core (tcgen05) MLP paths (hh_tcmlp.cu): near field in HH_BF16 mode
 // (work = target leaves) and K(r) for a list of separations.

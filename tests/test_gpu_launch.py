@@ -26,10 +26,11 @@ def ctx():
 
 
 def test_set_get_and_validation(ctx):
-    assert ctx.get_launch() == dict(small_max=0, aca_small_cps=0, aca_large_cps=0, near_cps=0)
-    ctx.set_launch(small_max=128, aca_small_cps=2, aca_large_cps=1, near_cps=8)
-    assert ctx.get_launch() == dict(small_max=128, aca_small_cps=2, aca_large_cps=1, near_cps=8)
-    for bad in (dict(small_max=16), dict(small_max=1024), dict(aca_small_cps=9), dict(near_cps=-1)):
+    assert ctx.get_launch() == dict(small_max=0, aca_small_cps=0, aca_large_cps=0, near_cps=0, rounds_min_cq=0)
+    ctx.set_launch(small_max=128, aca_small_cps=2, aca_large_cps=1, near_cps=8, rounds_min_cq=2048)
+    assert ctx.get_launch() == dict(small_max=128, aca_small_cps=2, aca_large_cps=1, near_cps=8, rounds_min_cq=2048)
+    for bad in (dict(small_max=16), dict(small_max=1024), dict(aca_small_cps=9), dict(near_cps=-1),
+                dict(rounds_min_cq=100)):
         with pytest.raises(hh.HHError):
             ctx.set_launch(**bad)
     assert ctx.get_launch()["small_max"] == 128     # unchanged by the rejected calls

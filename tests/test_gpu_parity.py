@@ -383,3 +383,31 @@ def test_predict_bf16_batch_equals_separate(ctx):
     for i in range(len(sizes)):
         Ui = ctx.predict(cuda(Xs[i]), cuda(Fs[i]), p).cpu().numpy()
         assert np.array_equal(Ub[off[i]:off[i + 1]], Ui)
+
+
+def test_bf16_rounds_independent_of_budget_and_j1_rule_1(ctx):
+    # The BF16 ACA runs as rounds over a set of active blocks whose size the
+    # memory budget sets; which blocks share a round must not change a bit of
+    # the result.  N = 30k has blocks from a few dozen up to thousands of rows.
+    n = 30000
+    X = cuda(hh_synth.rsa_cube(n, 0.1, seed=14))
+    F = cuda(hh_synth.forces(n, 8))
+    c = hh.Context()
+    c.set_mlp(THETA32, 32)
+    c.set_launch(rounds_min_cq=513)                      # every block with c or q > 512 through the rounds
+    U = c.predict(X, F, hh.Params(precision="bf16", leaf_size=64)).cpu().numpy()
+    rounds = c.stats()["n_aca_rounds"]
+    assert rounds > 0
+    Ub = c.predict(X, F, hh.Params(precision="bf16", leaf_size=64, mem_budget=16 << 20)).cpu().numpy()
+    assert c.stats()["n_aca_rounds"] > rounds            # fewer slots, more rounds
+    assert np.array_equal(U, Ub)
+    # the same blocks on CTA teams (the default threshold) agree within the BF16 tolerance
+    U0 = ctx.predict(X, F, hh.Params(precision="bf16", leaf_size=64)).cpu().numpy()
+    assert oracle.rel_error(U0, U) < 1e-4
+    # the randomised first column (rule 1) against the oracle's product with the same rule
+    n = 4096
+    Xh, Fh = hh_synth.rsa_cube(n, 0.1, seed=21), hh_synth.forces(n, 3)
+    p = hh.Params(precision="bf16", j1_rule=1, seed=5)
+    U1 = ctx.predict(cuda(Xh), cuda(Fh), p).cpu().numpy()
+    Uo, _ = oracle.hmatvec(Xh, Fh, kern(), leaf=32, eta=1.0, eps=1e-4, max_rank=48, j1_rule=1, seed=5)
+    assert oracle.rel_error(Uo, U1) < 1e-4
