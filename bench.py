@@ -19,21 +19,29 @@ value    = N * K / (sum of CUDA-event times of the K predictions), inputs
            256 MB buffer (outside the event pairs).
 e2e      = same metric through the same call with the inputs in pinned host
            memory: H2D copy of X and F, prediction, D2H copy of U, per step.
-rel_err  = Eq. 11 (M^(t,2) part only) against the FP64 dense oracle on 64
-           sampled target rows, with a bootstrap 95% interval over the rows
-           (rel_err_ci95); ms_per_step_min is the fastest timed step (rank 0).
-roofline = the ACA team kernels (the dominant stage).  BF16: algorithmic
-           tensor-core flops (2 x MACs of the MLP, 4736 per query for width 32)
-           / their event time, against the measured sustained bf16 peak
-           ("tensor" bound); roofline_near does the same for k_near_tc.
-           FP32 / FP64: FP32-equivalent flops (5145 per query) against the
-           FP32 FMA peak of 148 SMs x 128 lanes x 2 flop x 2.032 GHz =
-           77.0 TFLOP/s ("alu" bound).
+rel_err  = Eq. 11 (M^(t,2) part only) against the FP64 dense oracle on 512
+           sampled target rows, averaged over 5 force vectors (seeds 0..4),
+           with a bootstrap 95% interval over the rows (rel_err_ci95);
+           fp32 = the plain FP32 H-path on the same forces and rows (its
+           time per prediction and error); ms_per_step_min is the fastest
+           timed step (rank 0).
+roofline = the ACA kernels (the dominant stage).  BF16: the pair-kernel MLP
+           is bound by activation throughput: SiLU evaluations (96 per query
+           at width 32, one MUFU ex2 and one rcp each) per second of the ACA
+           phase against the SiLU rate hh_probe_throughput measures in the
+           same run ("alu" bound); "tensor" beside it gives the algorithmic
+           MMA flops (2 x MACs of the MLP, 4736 per query) against the
+           measured sustained bf16 peak; roofline_near does the same for
+           k_near_tc.  FP32 / FP64: FP32-equivalent flops (5145 per query)
+           against the measured FP32 FMA rate x 2.
 cpu_baseline = the FP64 CPU oracle as it stands: 64 sampled rows of the exact
            dense product on the host cores, scaled to particle-velocities/s.
 
 Under torchrun each rank runs its own independent suspension of N particles
-(weak scaling, no collective on the data path); rank 0 prints the line.
+(weak scaling, no collective on the data path); rank 0 prints the line.  With
+--scaling strong every rank predicts its shard of one suspension (blocks split
+by the W^G / W^H workloads of Section 3.3) and an NCCL all-reduce sums the
+partial velocities inside the timed step.
 
 --workload selects a further configuration, one line each (1 GPU):
   batch64      64 suspensions (cubes and Gaussian clouds) in one batched call
@@ -44,6 +52,9 @@ Under torchrun each rank runs its own independent suspension of N particles
   filament1m   20k straight chains of 50 beads (bond 2.2a, random
                orientation), explicit Euler steps: GPU bead forces (gravity,
                bonds, bending), prediction, position update
+  c2sweep      N = 100k, C_leaf 64: MLP 4-64-64-64-6 and RPY x FP64 / FP32 /
+               BF16 x eta in {0.7, 1, 1.5} x zeta in {1e-3, 1e-4, 1e-6}, one
+               line per cell with its error on 256 exact dense rows
   peaks        throughput of the units the pair-kernel MLP leans on (MUFU
                ex2 / rcp / tanh, FP32 and FP64 FMA, the epilogue SiLU), with
                the SM clock sampled meanwhile
@@ -67,6 +78,7 @@ FLOP_PER_QUERY = {32: 2 * (4 * 32 + 32 * 32 + 32 * 32 + 32 * 6) + 4 * 96 + 25,
 # tensor-core flops of one pair-kernel evaluation: 2 x the MACs of the four
 # MLP layers (the bf16 hi/lo operand split and padding are not counted)
 MMA_FLOP_PER_QUERY = {32: 2 * (4 * 32 + 32 * 32 + 32 * 32 + 32 * 6), 64: 2 * (4 * 64 + 64 * 64 + 64 * 64 + 64 * 6)}
+SILU_PER_QUERY = {32: 3 * 32, 64: 3 * 64}   # activations of the three hidden layers
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 PRECISION_NOTE = {
     "bf16": "pair-kernel MLP (near field and ACA rows/columns) on tcgen05, BF16 hi/lo operands, FP32 accumulate; "
@@ -161,6 +173,41 @@ def rel_err_ci95(ref, approx, reps=2000, seed=0):
     return [float(np.percentile(e, 2.5)), float(np.percentile(e, 97.5))]
 
 
+def rel_err_ci95_forces(ref, approx, reps=2000, seed=0):
+    """Bootstrap 95% interval of the Eq. 11 error averaged over force vectors:
+    ref, approx [nf, rows, 3]; target rows are resampled with replacement
+    (the same rows for every force vector) and the mean over the force
+    vectors of eps = sqrt(sum |dU_i|^2 / sum |U_i|^2) recomputed."""
+    num = np.sum((np.asarray(approx) - np.asarray(ref)) ** 2, axis=2)   # [nf, rows]
+    den = np.sum(np.asarray(ref) ** 2, axis=2)
+    pick = np.random.default_rng(seed).integers(0, num.shape[1], size=(reps, num.shape[1]))
+    e = np.sqrt(num[:, pick].sum(2) / den[:, pick].sum(2)).mean(0)
+    return [float(np.percentile(e, 2.5)), float(np.percentile(e, 97.5))]
+
+
+def shard_owners(cost, n_shards):
+    """The split of one prediction over n_shards GPUs (strong scaling): items
+    (admissible blocks by W^G = max(|tau|, |sigma|), target nodes by W^H =
+    |tau| sum |sigma|, Section 3.3) in order, cut into contiguous ranges of
+    equal cumulative cost; item i with cost w_i, exclusive prefix P_i and
+    total T goes to min(n - 1, floor(n (P_i + w_i / 2) / T)).  The library
+    applies the same rule on the device (hh_shard_owners)."""
+    cost = np.asarray(cost, dtype=np.float64)
+    T = cost.sum()
+    if T <= 0:
+        return np.zeros(len(cost), np.int32)
+    excl = np.concatenate([[0.0], np.cumsum(cost)[:-1]])
+    return np.minimum(np.floor(n_shards * (excl + 0.5 * cost) / T), n_shards - 1).astype(np.int32)
+
+
+def reduce_partial_u(U, dist):
+    """Strong scaling: every rank holds its shard's partial velocities of the
+    same suspension; their sum (all-reduce) is the prediction on every rank."""
+    if dist is not None and dist.is_available() and dist.is_initialized():
+        dist.all_reduce(U, op=dist.ReduceOp.SUM)
+    return U
+
+
 def weak_scaling_value(n_local, steps, total_ms_local, dist=None, device="cpu"):
     """Whole-job particle-velocities/s: the particles of every rank's own
     suspension over the slowest rank's time (max over ranks); returns
@@ -203,11 +250,11 @@ def run_reference(args, rank, world):
         cpu_baseline(X, F, theta, rows=8, seed=99)
     tot_rows, tot_t = 0, 0.0
     for s in range(args.steps):
-        _, _, rate, cores, dt = cpu_baseline(X, F, theta, rows=args.ref_rows, seed=s)
-        tot_rows += args.ref_rows
+        _, _, rate, cores, dt = cpu_baseline(X, F, theta, rows=args.cpu_rows, seed=s)
+        tot_rows += args.cpu_rows
         tot_t += dt
     v = tot_rows / tot_t
-    sample = f"{args.ref_rows} sampled target rows of the N={args.n} exact dense FP64 product per step"
+    sample = f"{args.cpu_rows} sampled target rows of the N={args.n} exact dense FP64 product per step"
     line = {"impl": "reference", "metric": metric_for(args.n), "value": v, "unit": "particle-velocities/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -229,21 +276,28 @@ def run_ours(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    X, F, theta = workload(args.n, seed_geom=1234 + rank)
+    strong = args.scaling == "strong" and world > 1
+    # weak: an independent suspension per rank; strong: one suspension, each rank its shard of the work
+    X, F, theta = workload(args.n, seed_geom=1234 if strong else 1234 + rank)
     n = len(X)
     ctx = hh.Context(dev)
     ctx.set_mlp(theta, 32)
     prec = args.precision
     p = hh.Params(leaf_size=args.leaf, eta=1.0, eps=args.eps, max_rank=48, precision=prec,
-                  mem_budget=args.budget_mb << 20)
+                  mem_budget=args.budget_mb << 20, shard_id=rank if strong else 0, n_shards=world if strong else 1)
     Xd = torch.as_tensor(X).cuda()
     Fd = torch.as_tensor(F).cuda()
     U = torch.empty_like(Xd)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     stream = torch.cuda.current_stream()
 
-    for _ in range(args.warmup):
+    def step():
         ctx.predict(Xd, Fd, p, out=U)
+        if strong:
+            reduce_partial_u(U, dist)   # NCCL all-reduce(sum) of the shards' FP64 partial velocities
+
+    for _ in range(args.warmup):
+        step()
     torch.cuda.synchronize()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -255,7 +309,7 @@ def run_ours(args, rank, world):
         for s in range(args.steps):
             flush.fill_(float(s))
             ev[s][0].record(stream)
-            ctx.predict(Xd, Fd, p, out=U)
+            step()
             ev[s][1].record(stream)
             st = ctx.stats()
             t_aca_kern += st.get("t_kernel_aca", st["t_aca"])
@@ -266,6 +320,8 @@ def run_ours(args, rank, world):
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     value, total_ms = weak_scaling_value(n, args.steps, float(np.sum(step_ms)), dist, "cuda")
+    if strong:   # the whole job predicted one suspension of n particles per step
+        value = n * args.steps / (total_ms / 1e3)
     clocks = clk.summary()
     st = ctx.stats()
     if args.profile:   # the timed predictions only (profiling runs): no accuracy, baseline or e2e legs
@@ -290,59 +346,101 @@ def run_ours(args, rank, world):
         t0 = time.perf_counter()
         Xd.copy_(Xh, non_blocking=True)
         Fd.copy_(Fh, non_blocking=True)
-        ctx.predict(Xd, Fd, p, out=U)
+        step()
         Uh.copy_(U, non_blocking=True)
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
-    e2e_value = n * world / float(np.mean(e2e_t))
+    e2e_value = n * (1 if strong else world) / float(np.mean(e2e_t))
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
 
-    # accuracy (Eq. 11 on M^(t,2) F) and the CPU baseline from the same sampled rows
+    # accuracy (Eq. 11 on M^(t,2) F, averaged over 5 force vectors) on ref_rows sampled target rows, and the
+    # plain FP32 H-path on the same forces (the "BF16 beats FP32 at equal accuracy" comparison)
+    import hh_synth
     import oracle
     a1 = oracle.self_mobility()
-    idx, Ud, cpu_rate, cores, cpu_dt = cpu_baseline(X, F, theta, rows=args.ref_rows)
-    Ug = Uh.numpy()[idx] - a1 * F[idx]
-    rel_err = float(oracle.rel_error(Ud, Ug))
+    Fs5 = np.stack([hh_synth.forces(n, sd) for sd in range(5)])
+    rows = np.sort(np.random.default_rng(0).choice(n, args.ref_rows, replace=False))
+
+    def predictions(prec):
+        pp = hh.Params(leaf_size=args.leaf, eta=1.0, eps=args.eps, max_rank=48, precision=prec,
+                       mem_budget=args.budget_mb << 20)
+        out, ms = [], []
+        for sd in range(5):
+            Fd.copy_(torch.as_tensor(Fs5[sd]))
+            flush.fill_(float(sd))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.predict(Xd, Fd, pp, out=U)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            out.append(U.cpu().numpy()[rows] - a1 * Fs5[sd][rows])
+        return np.stack(out), ms
+    Ug, _ = predictions(prec)
+    U32, ms32 = predictions("fp32") if prec != "fp32" else (Ug, [])
+    rates = measure_units(ctx)
+    idx, Ud1, cpu_rate, cores, cpu_dt = cpu_baseline(X, F, theta, rows=args.cpu_rows)
+    t0 = time.perf_counter()
+    Ud = oracle.dense_matvec_multi(X, Fs5, oracle.PairKernel("mlp", theta, 32), rows=rows, with_self=False)
+    ref_dt = time.perf_counter() - t0
+    errs = [float(oracle.rel_error(Ud[sd], Ug[sd])) for sd in range(5)]
+    errs32 = [float(oracle.rel_error(Ud[sd], U32[sd])) for sd in range(5)]
+    rel_err = float(np.mean(errs))
 
     peaks = _peaks()
     aca_ms = t_aca_kern / args.steps
     near_ms = st.get("t_kernel_near", st["t_near"])
     q_step = queries / args.steps
+    silu_rate = rates["silu"]
     if prec == "bf16":
-        # the ACA teams evaluate the MLP on tcgen05: algorithmic MMA flops against the measured bf16 peak
+        # the binding roofline of the pair-kernel MLP is activation throughput: SiLU evaluations (one ex2 and one
+        # rcp on the MUFU unit each, 96 per query at width 32) against the measured rate of the same SiLU
         peak, peak_src = peaks.get("bf16_tflops_sustained"), "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
         if peak is None:
             peak, peak_src = 1400.0, "fallback sustained bf16 1.4 PFLOP/s (of fallback)"
-        achieved = q_step * MMA_FLOP_PER_QUERY[32] / (aca_ms / 1e3) / 1e12
-        roofline = {"bound": "tensor", "kernel": "k_aca_tc (warp and CTA teams)", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": aca_traffic(q_step),
-                    "peak_source": peak_src}
+        silu_ach = q_step * SILU_PER_QUERY[32] / (aca_ms / 1e3) / 1e9
+        roofline = {"bound": "alu", "kernel": "ACA: k_aca_tc warp + CTA teams, k_round_tiles (largest blocks)",
+                    "achieved": silu_ach, "peak": silu_rate / 1e9, "unit": "G SiLU/s", "frac": silu_ach * 1e9 / silu_rate,
+                    "traffic": aca_traffic(q_step),
+                    "peak_source": "hh_probe_throughput SiLU rate measured in this run (MUFU ex2 + rcp per SiLU)",
+                    "tensor": {"achieved": q_step * MMA_FLOP_PER_QUERY[32] / (aca_ms / 1e3) / 1e12, "peak": peak,
+                               "unit": "TFLOP/s", "peak_source": peak_src}}
+        roofline["tensor"]["frac"] = roofline["tensor"]["achieved"] / peak
+        near_silu = st["n_near_pairs"] * SILU_PER_QUERY[32] / (near_ms / 1e3) / 1e9
         near_ach = st["n_near_pairs"] * MMA_FLOP_PER_QUERY[32] / (near_ms / 1e3) / 1e12
-        roofline_near = {"bound": "tensor", "kernel": "k_near_tc", "achieved": near_ach, "peak": peak,
-                         "unit": "TFLOP/s", "frac": near_ach / peak}
+        roofline_near = {"bound": "alu", "kernel": "k_near_tc", "achieved": near_silu, "peak": silu_rate / 1e9,
+                         "unit": "G SiLU/s", "frac": near_silu * 1e9 / silu_rate,
+                         "tensor": {"achieved": near_ach, "peak": peak, "unit": "TFLOP/s", "frac": near_ach / peak}}
     else:
         achieved = q_step * FLOP_PER_QUERY[32] / (aca_ms / 1e3) / 1e12
+        fma_peak = rates["ffma"] * 2 / 1e12
         roofline = {"bound": "alu", "kernel": "k_aca_cta + k_aca_warp (block ACA teams)", "achieved": achieved,
-                    "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                    "traffic": None,
-                    "peak_source": "derived: 148 SM x 128 FP32 lanes x 2 flop x 2.032 GHz (no measured FP32 peak)"}
+                    "peak": fma_peak, "unit": "TFLOP/s", "frac": achieved / fma_peak, "traffic": None,
+                    "peak_source": "hh_probe_throughput FP32 FMA rate measured in this run x 2 flop"}
         roofline_near = None
     line = {
         "metric": metric_for(n), "value": value, "unit": "particle-velocities/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong" if strong else "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16"}[prec], "data": "synthetic",
         "config": {"workload": f"uniform_cube_rsa_N{n}_phi0.1_mlp4-32-32-32-6", "n": n, "leaf_size": args.leaf,
                    "eta": 1.0, "eps": args.eps, "max_rank": 48, "precision": prec,
                    "arithmetic": PRECISION_NOTE[prec],
-                   "l2": "flushed between steps (256 MB write)", "parallelism": f"independent suspension per GPU"},
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": ("one suspension split over the GPUs by W^G / W^H, NCCL all-reduce of U"
+                                   if strong else "independent suspension per GPU")},
         "ms_per_step_min": float(np.min(step_ms)),
         "device_mem_gb": {"library_peak": st.get("mem_peak_bytes", -1) / 1e9,
                           "torch_peak": torch.cuda.max_memory_allocated() / 1e9},
-        "rel_err": rel_err, "rel_err_rows": len(idx), "rel_err_ci95": rel_err_ci95(Ud, Ug),
+        "rel_err": rel_err, "rel_err_rows": len(rows), "rel_err_forces": 5, "rel_err_per_force": errs,
+        "rel_err_ci95": rel_err_ci95_forces(Ud, Ug),
+        "fp32": {"ms_per_step": float(np.mean(ms32)) if ms32 else None, "rel_err": float(np.mean(errs32)),
+                 "rel_err_per_force": errs32, "note": "plain FP32 H-path (SIMT MLP) on the same 5 forces and rows"},
+        "units_per_s": rates,
         "stages_ms": {k: st[k] for k in ("t_tree", "t_part", "t_near", "t_aca", "t_acc")},
         "counts": {"n_aca_queries": st["n_aca_queries"], "n_near_pairs": st["n_near_pairs"],
                    "n_blocks_G": st["n_blocks_G"], "n_blocks_H": st["n_blocks_H"], "n_nodes": st["n_nodes"]},
@@ -350,6 +448,7 @@ def run_ours(args, rank, world):
         "roofline_near": roofline_near,
         "cpu_baseline": {"value": cpu_rate, "unit": "particle-velocities/s", "cores": cores, "kind": "oracle",
                          "sample": f"{len(idx)} target rows of the N={n} exact dense FP64 product ({cpu_dt:.1f} s)"},
+        "rel_err_reference": f"{len(rows)} rows x 5 forces of the exact dense FP64 product ({ref_dt:.1f} s)",
         "e2e": {"value": e2e_value, "unit": "particle-velocities/s", "h2d_bytes_per_step": 2 * 24 * n,
                 "d2h_bytes_per_step": 24 * n},
         "gpu_launches": launches,
@@ -424,7 +523,58 @@ def run_workload(args):
     a1 = oracle.self_mobility()
     line = {"n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "data": "synthetic"}
-    if args.workload == "peaks":
+    if args.workload == "c2sweep":
+        # N = 100k uniform cube, C_leaf 64, MLP 4-64-64-64-6 and the closed-form RPY tensor, FP64 / FP32 / BF16
+        # (BF16: the MLP only) x eta in {0.7, 1, 1.5} x zeta in {1e-3, 1e-4, 1e-6}; one line per cell
+        n = args.n if args.n != 1_000_000 else 100_000
+        X = hh_synth.rsa_cube(n, 0.1, seed=1234)
+        F = hh_synth.forces(n, 0)
+        th64 = hh_synth.mlp_params(64, 7)
+        c64 = hh.Context(dev)
+        c64.set_mlp(th64, 64)
+        Xd, Fd = torch.as_tensor(X).cuda(), torch.as_tensor(F).cuda()
+        U = torch.empty_like(Xd)
+        rows = np.sort(np.random.default_rng(3).choice(n, 256, replace=False))
+        refs = {}
+        for kind in ("mlp", "rpy"):
+            t0 = time.perf_counter()
+            refs[kind] = oracle.dense_matvec(X, F, oracle.PairKernel(kind, th64, 64), rows=rows, with_self=False)
+            refs[kind + "_s"] = time.perf_counter() - t0
+        for kind in ("mlp", "rpy"):
+            for prec in ("fp64", "fp32", "bf16"):
+                if kind == "rpy" and prec == "bf16":
+                    continue
+                for eta in (0.7, 1.0, 1.5):
+                    for eps in (1e-3, 1e-4, 1e-6):
+                        p = hh.Params(leaf_size=64, eta=eta, eps=eps, precision=prec, kernel=kind)
+                        c64.predict(Xd, Fd, p, out=U)
+                        torch.cuda.synchronize()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        c64.predict(Xd, Fd, p, out=U)
+                        e1.record()
+                        torch.cuda.synchronize()
+                        ms = e0.elapsed_time(e1)
+                        st = c64.stats()
+                        Ug = U.cpu().numpy()[rows] - a1 * F[rows]
+                        cell = dict(line)
+                        cell.update({"metric": "particle-velocities/sec, C2 sweep cell", "value": n / (ms / 1e3),
+                                     "unit": "particle-velocities/s", "ms_per_step": ms, "steps": 1, "warmup": 1,
+                                     "dtype": prec,
+                                     "config": {"workload": f"uniform_cube_rsa_N{n}_phi0.1_c2sweep", "n": n,
+                                                "kernel": "mlp4-64-64-64-6" if kind == "mlp" else "rpy",
+                                                "precision": prec, "eta": eta, "eps": eps, "leaf_size": 64},
+                                     "rel_err": float(oracle.rel_error(refs[kind], Ug)), "rel_err_rows": len(rows),
+                                     "n_aca_queries": st["n_aca_queries"], "n_near_pairs": st["n_near_pairs"],
+                                     "n_blocks_G": st["n_blocks_G"], "stages_ms": {k: st[k] for k in
+                                                                                  ("t_near", "t_aca")},
+                                     "gpu_launches": st.get("n_launches", 0)})
+                        print(json.dumps(cell), flush=True)
+        line.update({"metric": "C2 sweep finished", "value": len(rows), "unit": "rows", "ms_per_step": None,
+                     "dtype": "mixed", "config": {"workload": "c2sweep_summary",
+                                                  "reference_seconds": {k: refs[k + "_s"] for k in ("mlp", "rpy")}},
+                     "gpu_launches": 0, "clocks": None})
+    elif args.workload == "peaks":
         with ClockSampler(dev) as clk:
             rates = measure_units(ctx)
         line.update({"metric": "arithmetic-unit throughput (MUFU, FMA) on one B300",
@@ -585,15 +735,20 @@ def run_workload(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--eps", type=float, default=1e-4)
     ap.add_argument("--leaf", type=int, default=64)
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-rows", type=int, default=64)
+    ap.add_argument("--ref-rows", type=int, default=512,
+                    help="sampled target rows of the exact dense product for the accuracy (x 5 force vectors)")
+    ap.add_argument("--cpu-rows", type=int, default=64,
+                    help="sampled target rows the timed CPU baseline computes")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="under torchrun: weak = a suspension per GPU; strong = one suspension split over the GPUs")
     ap.add_argument("--budget-mb", type=int, default=0,
                     help="memory budget of the BF16 ACA's active blocks in MB (0 = the library default)")
     ap.add_argument("--profile", action="store_true",
@@ -601,7 +756,8 @@ def main():
     ap.add_argument("--clocks-csv", default=None,
                     help="keep the raw nvidia-smi clock samples of the timed region in this file")
     ap.add_argument("--workload", default="cube1m",
-                    choices=["cube1m", "batch64", "grad200k", "cube10m", "shortrange1m", "train", "filament1m", "peaks"],
+                    choices=["cube1m", "batch64", "grad200k", "cube10m", "shortrange1m", "train", "filament1m", "peaks",
+                             "c2sweep"],
                     help="cube1m is the headline; the others measure further configurations")
     args = ap.parse_args()
     if args.clocks_csv:

@@ -98,8 +98,11 @@ typedef struct {
     int32_t shard_id;    /* this shard's share of the block work lists                      */
     int32_t n_shards;    /* number of shards (1 = everything)                               */
     int32_t flags;       /* HH_FLAG_* bits, 0 = none                                        */
-    int64_t mem_budget;  /* bytes the BF16 block ACA may hold for its active blocks' factor
-                            workspaces (the query groups of Section 3.3); 0 = 8 GB         */
+    int64_t mem_budget;  /* bytes the admissible blocks of a call may hold beyond inputs,
+                            tree and partition (the bounded query groups of Section 3.3):
+                            half for one group's partial outputs, an eighth each for the
+                            warp- and CTA-team factor workspaces, a quarter for the round
+                            engine's active blocks; 0 = 32 GB                               */
 } hh_params;
 
 /* Fills *p with the defaults: leaf 32, eta 1, eps 1e-4, max_rank 48, FP32,
@@ -255,6 +258,15 @@ hh_status hh_export_tree(const hh_tree *tree, int32_t *perm, uint64_t *codes, in
  * buffers (NULL pointers skipped).  Synchronises the device. */
 hh_status hh_export_blocks(const hh_blocks *blocks, int32_t *PG, int64_t *nG, int32_t *PH, int64_t *nH);
 
+/* The split of the work over n_shards shards (hh_params.shard_id /
+ * n_shards; Section 3.3's workloads): block_owner[nG] receives the shard of
+ * each admissible block (cut into contiguous ranges of equal cumulative
+ * W^G = max(|tau|, |sigma|)), node_owner[n_nodes] the shard of each target
+ * node's inadmissible blocks (contiguous ranges of equal cumulative W^H =
+ * |tau| sum_sigma |sigma|).  Either pointer may be NULL (host buffers).
+ * Synchronises the device. */
+hh_status hh_shard_owners(const hh_blocks *blocks, int32_t n_shards, int32_t *block_owner, int32_t *node_owner);
+
 /* Copies the per-block ACA ranks ([nG]) and pivots ([nG, max_rank]
  * block-local row / column indices, -1 past the rank) to host buffers. */
 hh_status hh_export_aca(const hh_hmat *h, int32_t *ranks, int32_t *piv_rows, int32_t *piv_cols, int64_t *nG,
@@ -292,6 +304,9 @@ typedef struct {
                                precisions)                                   */
     double t_aca_tiles;     /* ms in the BF16 ACA's tile kernels (CUDA events) */
     double t_aca_steps;     /* ms in its step kernels (CUDA events)            */
+    int64_t n_aca_groups;   /* hh_predict: groups the admissible blocks ran in
+                               (their partial outputs within half of
+                               hh_params.mem_budget each)                    */
 } hh_stats_t;
 
 /* Short-range networks of Eq. 6 (Eq. 2 with the Eq. 4 normalisations; the

@@ -24,6 +24,7 @@ PINS = {
     "pair_block (MLP)": "SiLU pairs that make the network exactly affine; constant-output network against "
                         "scipy distances; block symmetry; width-32/64 layouts",
     "dense_matvec": "two-particle closed form; rows equal to dense_matrix products; RPY symmetry",
+    "dense_matvec_multi": "equals dense_matvec per force vector, bit for bit (same summation order)",
     "morton": "hand-derived codes for grid-aligned points",
     "tree": "Definition 1 invariants; hand-derived 1-D bisection",
     "partition": "exact cover of all (i, j); symmetry; brute-force admissibility over node pairs; "
@@ -90,6 +91,7 @@ def _declare(L):
         "or_self_mobility": (_D, [_D, _D]),
         "or_dense_matvec": (None, [_I, _P, _P, _P, _P, _I64, _I, _P]),
         "or_dense_matrix": (None, [_I, _P, _P, _I, _P]),
+        "or_dense_matvec_multi": (None, [_I, _P, _I, _P, _P, _P, _I64, _I, _P]),
         "or_dense_grad": (None, [_I, _P, _P, _P, _P, _I, _P, _P, _P]),
         "or_train_loss_grad": (_D, [_P, _I, _I64, _P, _P, _P, _D, _P]),
         "or_adam_step": (None, [_P, _P, _P, _P, _I64, _D, _D, _D, _D, _I]),
@@ -165,6 +167,20 @@ def dense_matvec(X, F, kernel: PairKernel, rows=None, with_self=True):
     else:
         U = np.zeros((n, 3))
         lib().or_dense_matvec(n, _ptr(X), _ptr(F), kernel.ref, None, n, int(with_self), _ptr(U))
+    return U
+
+
+def dense_matvec_multi(X, Fs, kernel: PairKernel, rows=None, with_self=True):
+    """dense_matvec for up to 8 force vectors Fs [nf, n, 3] at once (each pair
+    block evaluated once); returns [nf, rows or n, 3]."""
+    X = _f64(X); Fs = _f64(Fs)
+    n, nf = X.shape[0], Fs.shape[0]
+    if not 1 <= nf <= 8:
+        raise ValueError("1 to 8 force vectors")
+    r = np.ascontiguousarray(rows, dtype=np.int64) if rows is not None else None
+    nr = len(r) if r is not None else n
+    U = np.zeros((nf, nr, 3))
+    lib().or_dense_matvec_multi(n, _ptr(X), nf, _ptr(Fs), kernel.ref, _ptr(r), nr, int(with_self), _ptr(U))
     return U
 
 

@@ -202,6 +202,34 @@ void or_dense_matvec(int n, const double *X, const double *F, const or_kernel *k
     }
 }
 
+/* The same exact product for nf force vectors at once (F, U: [nf][n][3] and
+ * [nf][nrows][3]); each pair block is evaluated once and applied to every
+ * force vector, in the same order of j as or_dense_matvec. */
+void or_dense_matvec_multi(int n, const double *X, int nf, const double *F, const or_kernel *k, const int64_t *rows,
+                           int64_t nrows, int with_self, double *U)
+{
+    double a1 = or_self_mobility(k->a, k->mu);
+    if (!rows) nrows = n;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t t = 0; t < nrows; ++t) {
+        int64_t i = rows ? rows[t] : t;
+        double u[8][3] = {{0}};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double r[3] = {X[3 * i] - X[3 * j], X[3 * i + 1] - X[3 * j + 1], X[3 * i + 2] - X[3 * j + 2]};
+            double K[9];
+            or_pair_block(k, r, K);
+            for (int f = 0; f < nf; ++f) {
+                const double *Fj = F + 3 * ((size_t)f * n + j);
+                for (int a = 0; a < 3; ++a) u[f][a] += K[3 * a] * Fj[0] + K[3 * a + 1] * Fj[1] + K[3 * a + 2] * Fj[2];
+            }
+        }
+        for (int f = 0; f < nf; ++f)
+            for (int a = 0; a < 3; ++a)
+                U[3 * ((size_t)f * nrows + t) + a] = (with_self ? a1 * F[3 * ((size_t)f * n + i) + a] : 0.0) + u[f][a];
+    }
+}
+
 /* Dense 3n x 3n matrix (row-major, element (3i+a, 3j+b)). */
 void or_dense_matrix(int n, const double *X, const or_kernel *k, int with_self, double *M)
 {

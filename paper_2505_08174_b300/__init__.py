@@ -35,7 +35,7 @@ EXPORTS = [
     "hh_export_blocks", "hh_export_aca", "hh_export_factors", "hh_stats", "hh_tree_free", "hh_blocks_free", "hh_hmat_free",
     "hh_aca_block_apply_noalloc", "hh_eval_pairs", "hh_train_loss_grad", "hh_train_step",
     "hh_set_launch", "hh_get_launch", "hh_autotune", "hh_set_short_range", "hh_short_range",
-    "hh_filament_forces", "hh_filament_step", "hh_probe_throughput",
+    "hh_filament_forces", "hh_filament_step", "hh_probe_throughput", "hh_shard_owners",
 ]
 
 
@@ -61,7 +61,8 @@ class CStats(ctypes.Structure):
                 ("rank_hist", ctypes.c_int64 * 65), ("t_kernel_aca", ctypes.c_double),
                 ("t_kernel_near", ctypes.c_double), ("n_launches", ctypes.c_int64), ("t_short", ctypes.c_double),
                 ("n_short_pairs", ctypes.c_int64), ("mem_peak_bytes", ctypes.c_int64),
-                ("n_aca_rounds", ctypes.c_int64), ("t_aca_tiles", ctypes.c_double), ("t_aca_steps", ctypes.c_double)]
+                ("n_aca_rounds", ctypes.c_int64), ("t_aca_tiles", ctypes.c_double), ("t_aca_steps", ctypes.c_double),
+                ("n_aca_groups", ctypes.c_int64)]
 
 
 class CLaunch(ctypes.Structure):
@@ -112,6 +113,7 @@ def lib():
             "hh_export_aca": (st, [_P, _P, _P, _P, _P, _P]),
             "hh_export_factors": (st, [_P, _P, _P, _P, _P]),
             "hh_probe_throughput": (st, [_P, i32, ctypes.c_int64, _P, _P]),
+            "hh_shard_owners": (st, [_P, i32, _P, _P]),
             "hh_stats": (st, [_P, _P]),
             "hh_tree_free": (None, [_P]),
             "hh_blocks_free": (None, [_P]),
@@ -416,6 +418,17 @@ class Blocks(_Owned):
         self.ctx._check(lib().hh_export_blocks(self._h, G.ctypes.data_as(_P), None, H.ctypes.data_as(_P), None),
                         "hh_export_blocks")
         return G, H
+
+    def shard_owners(self, n_shards: int):
+        """(block_owner [nG], node_owner [n_nodes]): the shard of each admissible
+        block and of each target node's near field (see hh_shard_owners)."""
+        G, _ = self.export()
+        nn = self.tree.export()["begin"].shape[0]
+        bo = np.zeros(len(G), np.int32)
+        no = np.zeros(nn, np.int32)
+        self.ctx._check(lib().hh_shard_owners(self._h, int(n_shards), bo.ctypes.data_as(_P), no.ctypes.data_as(_P)),
+                        "hh_shard_owners")
+        return bo, no
 
 
 class HMatrix(_Owned):

@@ -233,7 +233,7 @@ __device__ void aca_block(const AcaArgs<R>& A, const Team& tm, S& sm, const R* t
             if (lane == 0) { sm.tv[3 * p] = a0; sm.tv[3 * p + 1] = a1; sm.tv[3 * p + 2] = a2; }
         }
         tm.sync();
-        R* out = A.part + 3 * A.pofs[b];
+        R* out = A.part + 3 * (A.pofs[b] - A.pofs_base);
         for (int i = 0; i < ROWS; ++i) {
             const int m = tid + SIZE * i;
             if (m >= c) break;
@@ -313,14 +313,14 @@ __global__ void __launch_bounds__(CTA_T) k_aca_cta(AcaArgs<R> A, int mode)
 
 // ---- work lists --------------------------------------------------------------
 __global__ void k_classify_blocks(const int32_t* __restrict__ PG, int64_t nG, const int32_t* __restrict__ nbeg,
-                                  const int32_t* __restrict__ nend, int shard, int n_shards, int small_max,
-                                  int64_t* __restrict__ small_flag, int64_t* __restrict__ large_flag,
+                                  const int32_t* __restrict__ nend, const uint8_t* __restrict__ shard_mine,
+                                  int64_t b0, int64_t b1, int small_max, int64_t* __restrict__ small_flag, int64_t* __restrict__ large_flag,
                                   uint64_t* __restrict__ large_key)
 {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nG) return;
     int32_t c = nend[PG[2 * b]] - nbeg[PG[2 * b]], q = nend[PG[2 * b + 1]] - nbeg[PG[2 * b + 1]];
-    bool mine = (b % n_shards) == shard;
+    bool mine = (shard_mine == nullptr || shard_mine[b]) && b >= b0 && b < b1;
     bool small = c <= small_max && q <= small_max;
     small_flag[b] = mine && small;
     large_flag[b] = mine && !small;
@@ -382,8 +382,9 @@ __global__ void k_class_bounds(const uint64_t* __restrict__ key, int64_t n, int6
 }
 
 template <typename R, int KIND>
-void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_small, const int32_t* work_large,
-                const std::vector<AcaClass>& cls, int max_small_cq, const hh_launch_cfg& lc, int mode, cudaStream_t s)
+void launch_aca(hh_ctx* ctx, const hh_params& p, AcaArgs<R> A, const int32_t* work_small, int64_t n_small,
+                const int32_t* work_large, const std::vector<AcaClass>& cls, int max_small_cq, const hh_launch_cfg& lc,
+                int mode, cudaStream_t s)
 {
     const int th_bytes = A.n_th * (int)sizeof(R);
     const int mr = std::min(A.max_rank, MAXR);
@@ -396,7 +397,7 @@ void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_
             // factors (max_rank x 9 x (c+q) reals) + c+q flag bytes, rounded to 256 B
             int64_t stride = (int64_t)k.max_cq * 9 * mr + ceil_div(k.max_cq, (int64_t)sizeof(R));
             stride = ceil_div(stride * (int64_t)sizeof(R), 256) * 256 / (int64_t)sizeof(R);
-            const int64_t budget = aca_workspace_budget();  // bytes of large-team workspace
+            const int64_t budget = budget_cta_teams(p);  // bytes of large-team workspace
             int64_t teams = std::min<int64_t>(k.end - k.begin, (int64_t)lc.aca_large_cps * ctx->n_sm);
             teams = std::max<int64_t>(1, std::min<int64_t>(teams, budget / (stride * (int64_t)sizeof(R))));
             R* scratch = dev_alloc_t<R>(stride * teams, s);
@@ -414,11 +415,12 @@ void launch_aca(hh_ctx* ctx, AcaArgs<R> A, const int32_t* work_small, int64_t n_
         ctx->kev_aca_used |= 1;
     }
     if (n_small > 0) {
-        int64_t blocks = std::min<int64_t>(ceil_div(n_small, WPB), (int64_t)lc.aca_small_cps * ctx->n_sm);
-        int64_t teams = blocks * WPB;
-        // factors (max_rank x 9 x (c+q) reals), rounded to 256 B
+        // factors (max_rank x 9 x (c+q) reals), rounded to 256 B; as many teams as the budget holds
         int64_t stride = (int64_t)std::min(max_small_cq, 2 * SMALL_MAX) * 9 * mr;
         stride = ceil_div(stride * (int64_t)sizeof(R), 256) * 256 / (int64_t)sizeof(R);
+        int64_t blocks = std::min<int64_t>(ceil_div(n_small, WPB), (int64_t)lc.aca_small_cps * ctx->n_sm);
+        blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, budget_warp_teams(p) / (stride * WPB * (int64_t)sizeof(R))));
+        int64_t teams = blocks * WPB;
         R* scratch = dev_alloc_t<R>(stride * teams, s);
         HH_CUDA(cudaMemsetAsync(A.counter + 1, 0, sizeof(unsigned long long), s));
         AcaArgs<R> B = A;
@@ -544,10 +546,12 @@ void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_para
     int64_t* tot = dev_alloc_t<int64_t>(2, s);
     const bool use_tc = p.precision == HH_BF16 && kernel_kind(p, ctx->width) < 2;
     const hh_launch_cfg lc = resolved_launch(ctx, use_tc);
-    k_classify_blocks<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(bl->PG, nG, t->nbeg, t->nend, p.shard_id,
-                                                                  p.n_shards, std::min(lc.small_max, SMALL_MAX), fs,
-                                                                  fl, key);
+    uint8_t* mine = shard_block_flags(t, bl, p, s);   // this shard's blocks (NULL: all)
+    k_classify_blocks<<<(unsigned)ceil_div(nG, 256), 256, 0, s>>>(bl->PG, nG, t->nbeg, t->nend, mine, r.b0,
+                                                                  r.b1 < 0 ? nG : r.b1, std::min(lc.small_max, SMALL_MAX),
+                                                                  fs, fl, key);
     HH_CHECK_LAUNCH();
+    if (mine) dev_free(mine, s);
     dev_scan_i64(fs, os, nG, tot, s);
     dev_scan_i64(fl, ol, nG, tot + 1, s);
     int64_t h[2];
@@ -629,9 +633,9 @@ void aca_run_t(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_para
             return;
         }
     }
-    if (kind == 0) launch_aca<R, 0>(ctx, A, ws, h[0], wl, cls, max_small_cq, lc, r.mode, s);
-    else if (kind == 1) launch_aca<R, 1>(ctx, A, ws, h[0], wl, cls, max_small_cq, lc, r.mode, s);
-    else launch_aca<R, 2>(ctx, A, ws, h[0], wl, cls, max_small_cq, lc, r.mode, s);
+    if (kind == 0) launch_aca<R, 0>(ctx, p, A, ws, h[0], wl, cls, max_small_cq, lc, r.mode, s);
+    else if (kind == 1) launch_aca<R, 1>(ctx, p, A, ws, h[0], wl, cls, max_small_cq, lc, r.mode, s);
+    else launch_aca<R, 2>(ctx, p, A, ws, h[0], wl, cls, max_small_cq, lc, r.mode, s);
     dev_free(fs, s); dev_free(fl, s); dev_free(os, s); dev_free(ol, s); dev_free(key, s); dev_free(tot, s);
     dev_free(ws, s); dev_free(wl, s);
 }

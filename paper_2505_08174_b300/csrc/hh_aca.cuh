@@ -37,6 +37,7 @@ struct AcaArgs {
     int32_t* pivJ;
     R* part;
     const int64_t* pofs;
+    int64_t pofs_base;     // block b's partial output at part + 3 * (pofs[b] - pofs_base)
     R* fac;
     const int64_t* fofs;
     unsigned* status;
@@ -259,6 +260,7 @@ AcaArgs<R> make_aca_args(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, con
     A.pivJ = r.pivJ;
     A.part = (R*)r.part;
     A.pofs = r.pofs;
+    A.pofs_base = r.pofs_base;
     A.fac = (R*)r.factors;
     A.fofs = r.fofs;
     A.status = ctx->d_status;

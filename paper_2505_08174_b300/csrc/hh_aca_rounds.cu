@@ -108,6 +108,7 @@ struct RoundArgs {
     int32_t* pivJ;
     float* part;
     const int64_t* pofs;
+    int64_t pofs_base;         // block b's partial output at part + 3 * (pofs[b] - pofs_base)
     float* fac;
     const int64_t* fofs;
     unsigned* status;
@@ -371,7 +372,7 @@ __device__ __forceinline__ void plain_seg(const RoundArgs& R, const SegView& g, 
                 y1 += cv[3] * tp[0] + cv[4] * tp[1] + cv[5] * tp[2];
                 y2 += cv[6] * tp[0] + cv[7] * tp[1] + cv[8] * tp[2];
             }
-            float* out = R.part + 3 * (R.pofs[g.b] + x);
+            float* out = R.part + 3 * (R.pofs[g.b] - R.pofs_base + x);
             out[0] = y0; out[1] = y1; out[2] = y2;
         }
     } else {   // mode 2: C [l][9][c] then Q [l][9][q] at fofs[b]
@@ -802,7 +803,7 @@ void aca_rounds_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh
 {
     HH_REQUIRE(p.kernel == HH_MLP && p.precision == HH_BF16, HH_ERR_ARG, "tensor-core ACA needs the BF16 MLP kernel");
     const int MR = std::min(p.max_rank, MAXR);
-    const int64_t budget = aca_budget_bytes(p);
+    const int64_t budget = budget_rounds(p);
     const int W = ctx->width;
     const size_t smem = W == 32 ? tile_smem_bytes<32>() : tile_smem_bytes<64>();
     if (W == 32) HH_CUDA(cudaFuncSetAttribute(k_round_tiles<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -843,6 +844,7 @@ void aca_rounds_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh
     R.pivJ = r.pivJ;
     R.part = (float*)r.part;
     R.pofs = r.pofs;
+    R.pofs_base = r.pofs_base;
     R.fac = (float*)r.factors;
     R.fofs = r.fofs;
     R.status = base.status;
@@ -972,9 +974,9 @@ void aca_rounds_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh
         HH_CUDA(cudaEventRecord(ctx->kev[3], s));
         ctx->kev_aca_used |= 2;
     }
-    ctx->stats.n_aca_rounds = rounds_total;
-    ctx->stats.t_aca_tiles = t_tiles;
-    ctx->stats.t_aca_steps = t_steps;
+    ctx->stats.n_aca_rounds += rounds_total;
+    ctx->stats.t_aca_tiles += t_tiles;
+    ctx->stats.t_aca_steps += t_steps;
     dev_free(next, s);
     dev_free(cnt, s);
     dev_free(lists, s);

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
                 if (lane == 0) { sm.tv[3 * p] = a0; sm.tv[3 * p + 1] = a1; sm.tv[3 * p + 2] = a2; }
             }
             tm.sync();
-            float* out = A.part + 3 * A.pofs[b];
+            float* out = A.part + 3 * (A.pofs[b] - A.pofs_base);
             for (int m = tid; m < c; m += SIZE) {
                 float y0 = 0.f, y1 = 0.f, y2 = 0.f;
                 for (int p = 0; p < l; ++p) {
@@ -439,9 +439,10 @@ void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_par
     } join_l{sl, s, ctx->join_ev, n_cls > 0}, join_r{sr, s, ctx->join2_ev, n_rounds > 0};
     if (n_small > 0) {
         constexpr int NT = TC_T / 32;
-        const int64_t blocks = std::min<int64_t>(ceil_div(n_small, NT), (int64_t)lc.aca_small_cps * ctx->n_sm);
         int64_t stride = (int64_t)std::min(max_small_cq, 2 * SMALL_MAX) * 9 * mr;
         stride = ceil_div(stride * (int64_t)sizeof(float), 256) * 256 / (int64_t)sizeof(float);
+        int64_t blocks = std::min<int64_t>(ceil_div(n_small, NT), (int64_t)lc.aca_small_cps * ctx->n_sm);
+        blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, budget_warp_teams(p) / (stride * NT * (int64_t)sizeof(float))));
         float* scratch = dev_alloc_t<float>(stride * blocks * NT, s);
         HH_CUDA(cudaMemsetAsync(A.counter + 1, 0, sizeof(unsigned long long), s));
         AcaArgs<float> B = A;
@@ -458,7 +459,7 @@ void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_par
         const AcaClass& k = cls[i];
         int64_t stride = (int64_t)k.max_cq * 9 * mr + ceil_div(k.max_cq, (int64_t)sizeof(float));
         stride = ceil_div(stride * (int64_t)sizeof(float), 256) * 256 / (int64_t)sizeof(float);
-        const int64_t budget = aca_budget_bytes(p);
+        const int64_t budget = budget_cta_teams(p);
         int64_t teams = std::min<int64_t>(k.end - k.begin, (int64_t)lc.aca_large_cps * ctx->n_sm);
         teams = std::max<int64_t>(1, std::min<int64_t>(teams, budget / (stride * (int64_t)sizeof(float))));
         float* scratch = dev_alloc_t<float>(stride * teams, sl);
@@ -472,8 +473,6 @@ void aca_tc_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh_par
         else launch_tc<64, CtaTeamT<TC_T>>(ctx, B, teams, r.mode, sl);
         dev_free(scratch, sl);
     }
-    ctx->stats.n_aca_rounds = 0;
-    ctx->stats.t_aca_tiles = ctx->stats.t_aca_steps = 0.0;
     if (n_rounds > 0) aca_rounds_run(ctx, t, bl, p, r, work_rounds, rcls_begin, rcls_max_cq, n_rcls, sr, false);
     join_l.now();
     join_r.now();

@@ -134,6 +134,9 @@ void reset_call(hh_ctx* ctx, cudaStream_t s)
     ctx->kev_aca_used = 0;
     ctx->kev_near_used = 0;
     ctx->launch_base = g_hh_launches;
+    ctx->stats.n_aca_rounds = 0;
+    ctx->stats.t_aca_tiles = ctx->stats.t_aca_steps = 0.0;
+    ctx->stats.n_aca_groups = 0;
 }
 
 // Kernel event times and the launch count of the call (after a stream sync).
@@ -509,22 +512,45 @@ hh_status hh_predict(hh_ctx* ctx, const double* X_dev, const double* F_dev, cons
             HH_CUDA(cudaEventRecord(ev[7], s));
         }
         HH_CUDA(cudaEventRecord(ev[3], s));
+        // the admissible blocks in groups whose partial outputs fit their share
+        // of the memory budget, each folded into the FP64 sum before the next
         int64_t* pofs = dev_alloc_t<int64_t>(b->nG + 1, s);
-        int64_t total = partial_offsets(t, b, 0, pofs, s);
-        void* part = dev_alloc(rb * 3 * (size_t)(total > 0 ? total : 1), s);
-        // blocks of other shards are not written by this call
-        if (p->n_shards > 1) HH_CUDA(cudaMemsetAsync(part, 0, rb * 3 * (size_t)(total > 0 ? total : 1), s));
-        AcaRun r;
-        r.Fs = Fs;
-        r.part = part;
-        r.pofs = pofs;
-        r.mode = 0;
-        aca_run(ctx, t, b, *p, r, s);
+        const int64_t total = partial_offsets(t, b, 0, pofs, s);
+        double* Us = dev_alloc_t<double>(3 * t->n, s);
+        const double a1 = p->shard_id == 0 ? alpha1(*p) : 0.0;
+        accumulate_begin(t, *p, Fs, y, a1, Us, s);
+        std::vector<int64_t> pofs_at;
+        const auto groups = block_groups(b, pofs, total, budget_partials(*p) / (3 * rb), &pofs_at, s);
+        double aca_kernel_ms = 0.0;
+        for (size_t g = 0; g < groups.size(); ++g) {
+            const int64_t len = pofs_at[g + 1] - pofs_at[g];
+            void* part = dev_alloc(rb * 3 * (size_t)(len > 0 ? len : 1), s);
+            // blocks of other shards are not written by this call
+            if (p->n_shards > 1) HH_CUDA(cudaMemsetAsync(part, 0, rb * 3 * (size_t)(len > 0 ? len : 1), s));
+            AcaRun r;
+            r.Fs = Fs;
+            r.part = part;
+            r.pofs = pofs;
+            r.pofs_base = pofs_at[g];
+            r.b0 = groups[g].first;
+            r.b1 = groups[g].second;
+            r.mode = 0;
+            ctx->kev_aca_used = 0;
+            aca_run(ctx, t, b, *p, r, s);
+            accumulate_group(t, *p, part, pofs, pofs_at[g], b->rowG, groups[g].first, groups[g].second, Us, s);
+            dev_free(part, s);
+            if (ctx->kev_aca_used & 2) {   // this group's ACA kernels (the events are reused by the next)
+                float ms = 0.f;
+                HH_CUDA(cudaEventSynchronize(ctx->kev[3]));
+                HH_CUDA(cudaEventElapsedTime(&ms, ctx->kev[2], ctx->kev[3]));
+                aca_kernel_ms += ms;
+            }
+        }
+        ctx->kev_aca_used = 0;
         HH_CUDA(cudaEventRecord(ev[4], s));
-        double a1 = p->shard_id == 0 ? alpha1(*p) : 0.0;
-        accumulate_impl(ctx, t, *p, Fs, y, b->nG > 0 ? part : nullptr, pofs, b->rowG, nullptr, a1, U_dev, s);
+        accumulate_end(t, Us, U_dev, s);
         HH_CUDA(cudaEventRecord(ev[5], s));
-        dev_free(part, s);
+        dev_free(Us, s);
         dev_free(pofs, s);
         dev_free(y, s);
         dev_free(Fs, s);
@@ -549,7 +575,9 @@ hh_status hh_predict(hh_ctx* ctx, const double* X_dev, const double* F_dev, cons
         HH_CUDA(cudaMemcpy(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost));
         ctx->stats.n_aca_queries = (int64_t)cnt[4];
         ctx->stats.n_near_pairs = (int64_t)cnt[5];
+        ctx->stats.n_aca_groups = (int64_t)groups.size();
         finish_stats(ctx);
+        ctx->stats.t_kernel_aca = aca_kernel_ms;
         return w;
     });
     free_blocks(b);

@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(32) k_far_bwd(const double* __restrict__ Xs, c
                                                 int64_t nG, const int32_t* __restrict__ nbeg,
                                                 const int32_t* __restrict__ nend, const int32_t* __restrict__ rank,
                                                 const int32_t* __restrict__ pivI, const int32_t* __restrict__ pivJ,
-                                                int max_rank, int shard, int n_shards, const R* __restrict__ fac,
+                                                int max_rank, const uint8_t* __restrict__ mine, const R* __restrict__ fac,
                                                 const int64_t* __restrict__ fofs, const R* __restrict__ th_g, R a,
                                                 R* __restrict__ scratch, int64_t ws_stride,
                                                 const int32_t* __restrict__ perm, double* gX, double* gth, R* gacc,
@@ -416,7 +416,7 @@ __global__ void __launch_bounds__(32) k_far_bwd(const double* __restrict__ Xs, c
     R* Cb = scratch + (int64_t)blockIdx.x * ws_stride;
     R* Cw = Cb + ws_stride / 2;   // rebuilt factors when the H-matrix holds pivots only
     for (int64_t b = blockIdx.x; b < nG; b += gridDim.x) {
-        if (b % n_shards != shard) continue;
+        if (mine && !mine[b]) continue;
         const int l = rank[b];
         if (l <= 0) continue;
         const int32_t t = PG[2 * b], s = PG[2 * b + 1];
@@ -610,11 +610,11 @@ __global__ void k_theta_out(const double* __restrict__ in, float* __restrict__ o
     if (i < n) out[i] += (float)in[i];
 }
 
-__global__ void k_leafs(const int32_t* __restrict__ child, int32_t n, int shard, int n_shards, int32_t* out,
+__global__ void k_leafs(const int32_t* __restrict__ child, int32_t n, const uint8_t* __restrict__ mine, int32_t* out,
                         int* count)
 {
     const int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n && child[2 * t] < 0 && t % n_shards == shard) out[atomicAdd(count, 1)] = t;
+    if (t < n && child[2 * t] < 0 && (mine == nullptr || mine[t])) out[atomicAdd(count, 1)] = t;
 }
 
 template <typename R, int W>
@@ -634,9 +634,10 @@ void launch_bwd(hh_ctx* ctx, const hh_hmat* h, const double* Fs, const double* W
     int32_t* leaves = dev_alloc_t<int32_t>(t->n_nodes, s);
     int* cnt = dev_alloc_t<int>(1, s);
     HH_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int), s));
-    k_leafs<<<(unsigned)ceil_div(t->n_nodes, 256), 256, 0, s>>>(t->child, t->n_nodes, p.shard_id, p.n_shards, leaves,
-                                                                cnt);
+    uint8_t* node_mine = shard_node_flags(t, b, p, s);
+    k_leafs<<<(unsigned)ceil_div(t->n_nodes, 256), 256, 0, s>>>(t->child, t->n_nodes, node_mine, leaves, cnt);
     HH_CHECK_LAUNCH();
+    if (node_mine) dev_free(node_mine, s);
     int n_leaves = 0;
     HH_CUDA(cudaMemcpyAsync(&n_leaves, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
     HH_CUDA(cudaStreamSynchronize(s));
@@ -663,11 +664,13 @@ void launch_bwd(hh_ctx* ctx, const hh_hmat* h, const double* Fs, const double* W
         int64_t grid = std::min<int64_t>(b->nG, max_grid);
         grid = std::max<int64_t>(1, std::min<int64_t>(grid, budget / (stride * (int64_t)sizeof(R))));
         R* scratch = dev_alloc_t<R>(grid * stride, s);
+        uint8_t* mine = shard_block_flags(t, b, p, s);
         k_far_bwd<R, W><<<(unsigned)grid, 32, smem, s>>>(t->Xs, Fs, Ws, b->PG, b->nG, t->nbeg, t->nend, h->rank,
-                                                        h->pivI, h->pivJ, p.max_rank, p.shard_id, p.n_shards,
+                                                        h->pivI, h->pivJ, p.max_rank, mine,
                                                         (const R*)h->factors, h->fofs, th, (R)p.radius, scratch,
                                                         stride, t->perm, gX, gth, gacc, gFs);
         HH_CHECK_LAUNCH();
+        if (mine) dev_free(mine, s);
         dev_free(scratch, s);
     }
     dev_free(leaves, s);

@@ -127,6 +127,12 @@ void free_hmat(hh_hmat* h);
 // of source node s in order.
 void source_index(const hh_tree* t, const hh_blocks* b, int32_t* order, int64_t* col, cudaStream_t s);
 
+// This shard's share of the work (hh_shard.cu; NULL when n_shards == 1):
+// flags[nG] over the admissible blocks, flags[n_nodes] over the target nodes
+// of the near field.  Stream-ordered allocations the caller frees.
+uint8_t* shard_block_flags(const hh_tree* t, const hh_blocks* b, const hh_params& p, cudaStream_t s);
+uint8_t* shard_node_flags(const hh_tree* t, const hh_blocks* b, const hh_params& p, cudaStream_t s);
+
 // Gather rows of an [n,3] FP64 array into sorted order: out[m] = in[perm[m]].
 void gather_rows(const double* in, const int32_t* perm, int64_t n, double* out, cudaStream_t s);
 
@@ -141,8 +147,10 @@ void near_field(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_para
 // factors at fofs.
 struct AcaRun {
     const double* Fs = nullptr;   // sorted forces (mode 0)
-    void* part = nullptr;         // per-block partial outputs (mode 0)
+    void* part = nullptr;         // per-block partial outputs (mode 0), block b at 3 * (pofs[b] - pofs_base)
     const int64_t* pofs = nullptr;
+    int64_t pofs_base = 0;
+    int64_t b0 = 0, b1 = -1;      // the admissible blocks of this run: [b0, b1) (b1 < 0: to the end)
     int32_t* rank = nullptr;
     int32_t* pivI = nullptr;
     int32_t* pivJ = nullptr;
@@ -162,18 +170,16 @@ struct AcaClass {
     int32_t max_cq;
 };
 
-// Bytes the CTA-team ACA launches may take for their factor workspaces: half
-// of the device memory free at the time, at least 4 GB (grids shrink to fit).
-inline int64_t aca_workspace_budget()
-{
-    size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return (int64_t)24 << 30;
-    return std::max<int64_t>((int64_t)4 << 30, (int64_t)(fr / 2));
-}
-
-// Bytes the BF16 block ACA may hold for its active blocks (hh_params.mem_budget,
-// default 8 GB).
-inline int64_t aca_budget_bytes(const hh_params& p) { return p.mem_budget > 0 ? p.mem_budget : (int64_t)8 << 30; }
+// The device memory a prediction's admissible blocks may hold beyond the
+// inputs, the tree and the partition (hh_params.mem_budget, default 32 GB),
+// and its shares: the per-block partial outputs of one group of blocks (1/2),
+// the warp teams' and the CTA teams' factor workspaces (1/8 each), the round
+// engine's active blocks (1/4).
+inline int64_t aca_budget_bytes(const hh_params& p) { return p.mem_budget > 0 ? p.mem_budget : (int64_t)32 << 30; }
+inline int64_t budget_partials(const hh_params& p) { return aca_budget_bytes(p) / 2; }
+inline int64_t budget_warp_teams(const hh_params& p) { return aca_budget_bytes(p) / 8; }
+inline int64_t budget_cta_teams(const hh_params& p) { return aca_budget_bytes(p) / 8; }
+inline int64_t budget_rounds(const hh_params& p) { return aca_budget_bytes(p) / 4; }
 
 inline int* ctx_pinned_int(hh_ctx* ctx) { return ctx->h_pinned; }
 
@@ -243,6 +249,23 @@ void lowrank_apply(hh_ctx* ctx, const hh_hmat* h, const double* Fs, void* part, 
 void accumulate_impl(hh_ctx* ctx, const hh_tree* t, const hh_params& p, const double* Fs, const void* y_near,
                      const void* part, const int64_t* pofs, const int64_t* rowG, const int32_t* order, double alpha1,
                      double* U, cudaStream_t s);
+
+// The same sum in steps, for a prediction whose admissible blocks run in
+// groups (bounded partial-output memory): Us (sorted, FP64 [n,3]) =
+// alpha1 F + y_near; then, per group [b0, b1), the group's partials (block b
+// at part + 3 (pofs[b] - pofs_base)); finally U[perm[m]] = Us[m].  Each
+// particle's terms are added in k_accum's order, so the grouping changes no
+// bit of U.
+void accumulate_begin(const hh_tree* t, const hh_params& p, const double* Fs, const void* y_near, double alpha1,
+                      double* Us, cudaStream_t s);
+void accumulate_group(const hh_tree* t, const hh_params& p, const void* part, const int64_t* pofs, int64_t pofs_base,
+                      const int64_t* rowG, int64_t b0, int64_t b1, double* Us, cudaStream_t s);
+void accumulate_end(const hh_tree* t, const double* Us, double* U, cudaStream_t s);
+// Contiguous groups of admissible blocks whose partial outputs hold at most
+// about cap entries each (a group starts at each multiple of cap); pofs_at
+// receives each group's first offset and, last, the total.  Synchronises.
+std::vector<std::pair<int64_t, int64_t>> block_groups(const hh_blocks* b, const int64_t* pofs, int64_t total,
+                                                      int64_t cap, std::vector<int64_t>* pofs_at, cudaStream_t s);
 
 // Partial-output offsets: pofs[b] = sum_{b' < b} |target(b')| (or source if
 // transpose); returns the total (synchronises).

@@ -94,12 +94,13 @@ __global__ void __launch_bounds__(32 * NEAR_WPB) k_near(const double* __restrict
     }
 }
 
-// Leaves of this shard: flag[t] = 1 for leaf nodes with (t mod shards == shard).
-__global__ void k_leaf_flags(const int32_t* __restrict__ child, int32_t n_nodes, int shard, int n_shards,
+// Leaves of this shard: flag[t] = 1 for leaf nodes this shard owns (all
+// leaves when mine is NULL).
+__global__ void k_leaf_flags(const int32_t* __restrict__ child, int32_t n_nodes, const uint8_t* __restrict__ mine,
                              int64_t* __restrict__ flag)
 {
     int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n_nodes) flag[t] = child[2 * t] < 0 && (t % n_shards) == shard;
+    if (t < n_nodes) flag[t] = child[2 * t] < 0 && (mine == nullptr || mine[t]);
 }
 
 __global__ void k_compact32(const int64_t* __restrict__ flag, const int64_t* __restrict__ off, int64_t n,
@@ -191,8 +192,10 @@ void near_field(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_para
     int64_t* flag = dev_alloc_t<int64_t>(nn, s);
     int64_t* off = dev_alloc_t<int64_t>(nn, s);
     int64_t* tot = dev_alloc_t<int64_t>(1, s);
-    k_leaf_flags<<<(unsigned)ceil_div(nn, 256), 256, 0, s>>>(t->child, nn, p.shard_id, p.n_shards, flag);
+    uint8_t* mine = shard_node_flags(t, b, p, s);
+    k_leaf_flags<<<(unsigned)ceil_div(nn, 256), 256, 0, s>>>(t->child, nn, mine, flag);
     HH_CHECK_LAUNCH();
+    if (mine) dev_free(mine, s);
     dev_scan_i64(flag, off, nn, tot, s);
     int64_t n_work = 0;
     HH_CUDA(cudaMemcpyAsync(&n_work, tot, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -267,6 +270,86 @@ void eval_pairs_simt(hh_ctx* ctx, const hh_params& p, const double* r, int64_t n
     }
 }
 
+// Us[m] = alpha1 F_m + y_near(m) (sorted order, FP64): the first terms of
+// k_accum's sum, to which the partials of the groups of blocks are added.
+template <typename R>
+__global__ void k_accum_begin(int64_t n, const double* __restrict__ Fs, const R* __restrict__ ynear, double a1,
+                              double* __restrict__ Us)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    for (int u = 0; u < 3; ++u) {
+        double v = a1 * Fs[3 * m + u];
+        if (ynear) v += (double)ynear[3 * m + u];
+        Us[3 * m + u] = v;
+    }
+}
+
+// Us[m] += the partial outputs of the admissible blocks b0 <= b < b1 that
+// contain m, in increasing b -- root to leaf, sources ascending: the order of
+// k_accum, so a grouped prediction adds the same terms in the same order.
+template <typename R>
+__global__ void k_accum_group(int64_t n, const R* __restrict__ part, const int64_t* __restrict__ pofs,
+                              int64_t pofs_base, const int64_t* __restrict__ rowG, int64_t b0, int64_t b1,
+                              const int32_t* __restrict__ child, const int32_t* __restrict__ nbeg,
+                              const int32_t* __restrict__ nend, const int64_t* __restrict__ off, int B,
+                              double* __restrict__ Us)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= m) lo = mid; else hi = mid - 1;
+    }
+    double u0 = Us[3 * m], u1 = Us[3 * m + 1], u2 = Us[3 * m + 2];
+    int32_t node = lo;
+    for (;;) {
+        const int64_t r0 = max(rowG[node], b0), r1 = min(rowG[node + 1], b1);
+        const int64_t loc = m - nbeg[node];
+        for (int64_t k = r0; k < r1; ++k) {
+            const R* pb = part + 3 * (pofs[k] - pofs_base + loc);
+            u0 += (double)pb[0];
+            u1 += (double)pb[1];
+            u2 += (double)pb[2];
+        }
+        const int32_t c0 = child[2 * node];
+        if (c0 < 0) break;
+        node = m < nend[c0] ? c0 : child[2 * node + 1];
+    }
+    Us[3 * m] = u0;
+    Us[3 * m + 1] = u1;
+    Us[3 * m + 2] = u2;
+}
+
+__global__ void k_accum_end(int64_t n, const double* __restrict__ Us, const int32_t* __restrict__ perm,
+                            double* __restrict__ U)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const int64_t dst = perm[m];
+    for (int u = 0; u < 3; ++u) U[3 * dst + u] = Us[3 * m + u];
+}
+
+// First blocks of the groups: cut[k] = the first block whose partial output
+// starts at or after k * cap (k = 0 .. n_groups), and the partial offsets
+// there (pofs_at[k]; the total past the last block).
+__global__ void k_group_cuts(const int64_t* __restrict__ pofs, int64_t nG, int64_t total, int64_t cap, int n_groups,
+                             int64_t* __restrict__ cut, int64_t* __restrict__ pofs_at)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > n_groups) return;
+    int64_t lo = 0, hi = nG;   // first b with pofs[b] >= k * cap (nG if none)
+    const int64_t thr = (int64_t)k * cap;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (pofs[mid] >= thr) hi = mid; else lo = mid + 1;
+    }
+    if (k == n_groups) lo = nG;
+    cut[k] = lo;
+    pofs_at[k] = lo < nG ? pofs[lo] : total;
+}
+
 int64_t partial_offsets(const hh_tree* t, const hh_blocks* b, int transpose, int64_t* pofs, cudaStream_t s)
 {
     const int64_t nG = b->nG;
@@ -298,4 +381,60 @@ void accumulate_impl(hh_ctx* ctx, const hh_tree* t, const hh_params& p, const do
         k_accum<float><<<grid, 256, 0, s>>>(n, Fs, (const float*)y_near, (const float*)part, pofs, rowG, order,
                                             t->child, t->nbeg, t->nend, t->d_offsets, t->batch, t->perm, alpha1, U);
     HH_CHECK_LAUNCH();
+}
+
+void accumulate_begin(const hh_tree* t, const hh_params& p, const double* Fs, const void* y_near, double alpha1,
+                      double* Us, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)ceil_div(t->n, 256);
+    if (real_bytes(p) == 8) k_accum_begin<double><<<grid, 256, 0, s>>>(t->n, Fs, (const double*)y_near, alpha1, Us);
+    else k_accum_begin<float><<<grid, 256, 0, s>>>(t->n, Fs, (const float*)y_near, alpha1, Us);
+    HH_CHECK_LAUNCH();
+}
+
+void accumulate_group(const hh_tree* t, const hh_params& p, const void* part, const int64_t* pofs, int64_t pofs_base,
+                      const int64_t* rowG, int64_t b0, int64_t b1, double* Us, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)ceil_div(t->n, 256);
+    if (real_bytes(p) == 8)
+        k_accum_group<double><<<grid, 256, 0, s>>>(t->n, (const double*)part, pofs, pofs_base, rowG, b0, b1, t->child,
+                                                   t->nbeg, t->nend, t->d_offsets, t->batch, Us);
+    else
+        k_accum_group<float><<<grid, 256, 0, s>>>(t->n, (const float*)part, pofs, pofs_base, rowG, b0, b1, t->child,
+                                                  t->nbeg, t->nend, t->d_offsets, t->batch, Us);
+    HH_CHECK_LAUNCH();
+}
+
+void accumulate_end(const hh_tree* t, const double* Us, double* U, cudaStream_t s)
+{
+    k_accum_end<<<(unsigned)ceil_div(t->n, 256), 256, 0, s>>>(t->n, Us, t->perm, U);
+    HH_CHECK_LAUNCH();
+}
+
+std::vector<std::pair<int64_t, int64_t>> block_groups(const hh_blocks* b, const int64_t* pofs, int64_t total,
+                                                      int64_t cap, std::vector<int64_t>* pofs_at, cudaStream_t s)
+{
+    const int64_t nG = b->nG;
+    std::vector<std::pair<int64_t, int64_t>> g;
+    pofs_at->clear();
+    if (nG == 0) return g;
+    cap = std::max<int64_t>(1, cap);
+    const int ng = (int)std::min<int64_t>(ceil_div(std::max<int64_t>(total, 1), cap), 1 << 20);
+    int64_t* cut = dev_alloc_t<int64_t>(ng + 1, s);
+    int64_t* pa = dev_alloc_t<int64_t>(ng + 1, s);
+    k_group_cuts<<<(unsigned)ceil_div(ng + 1, 256), 256, 0, s>>>(pofs, nG, total, cap, ng, cut, pa);
+    HH_CHECK_LAUNCH();
+    std::vector<int64_t> hc(ng + 1), hp(ng + 1);
+    HH_CUDA(cudaMemcpyAsync(hc.data(), cut, sizeof(int64_t) * (ng + 1), cudaMemcpyDeviceToHost, s));
+    HH_CUDA(cudaMemcpyAsync(hp.data(), pa, sizeof(int64_t) * (ng + 1), cudaMemcpyDeviceToHost, s));
+    HH_CUDA(cudaStreamSynchronize(s));
+    dev_free(cut, s);
+    dev_free(pa, s);
+    for (int k = 0; k < ng; ++k)
+        if (hc[k + 1] > hc[k]) {
+            g.emplace_back(hc[k], hc[k + 1]);
+            pofs_at->push_back(hp[k]);
+        }
+    if (!g.empty()) pofs_at->push_back(hp[ng]);
+    return g;
 }

@@ -240,6 +240,38 @@ def test_shards_sum_to_whole(ctx):
     assert oracle.rel_error(full, sum(parts)) < 1e-14
 
 
+def test_shard_split_is_cost_balanced():
+    import bench
+    # N = 100k, C_leaf 64: the split the shards use equals the definition, is
+    # contiguous, and each shard's W^G / W^H is within one item of the mean
+    c = hh.Context()
+    c.set_mlp(THETA32, 32)
+    n = 100000
+    X = hh_synth.rsa_cube(n, 0.1, seed=17)
+    p = hh.Params(precision="bf16", leaf_size=64)
+    t = c.build_tree(cuda(X), p)
+    b = c.partition(t, p)
+    G, H = b.export()
+    te = t.export()
+    size = (te["end"] - te["begin"]).astype(np.int64)
+    wg = np.maximum(size[G[:, 0]], size[G[:, 1]])
+    wh = np.zeros(len(size), np.int64)
+    np.add.at(wh, H[:, 0], size[H[:, 0]] * size[H[:, 1]])
+    for ns in (2, 3, 8):
+        bo, no = b.shard_owners(ns)
+        assert np.array_equal(bo, bench.shard_owners(wg, ns)) and np.array_equal(no, bench.shard_owners(wh, ns))
+        assert np.all(np.diff(bo) >= 0) and np.all(np.diff(no) >= 0)
+        for own, w in ((bo, wg), (no, wh)):
+            per = np.bincount(own, weights=w, minlength=ns)
+            assert np.all(np.abs(per - w.sum() / ns) <= w.max()), per
+    # the BF16 prediction splits into shards that sum to the whole (to FP32 rounding of the sum)
+    F = hh_synth.forces(n, 2)
+    full = c.predict(cuda(X), cuda(F), p).cpu().numpy()
+    parts = [c.predict(cuda(X), cuda(F), hh.Params(precision="bf16", leaf_size=64, shard_id=s, n_shards=4))
+             .cpu().numpy() for s in range(4)]
+    assert oracle.rel_error(full, sum(parts)) < 1e-12
+
+
 def test_batch_predict_equals_separate(ctx):
     sizes = [900, 1300, 2]
     Xs = [hh_synth.rsa_cube(s, 0.1, seed=20 + i) for i, s in enumerate(sizes)]

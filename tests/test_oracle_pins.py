@@ -508,3 +508,16 @@ def test_train_loss_grad_and_adam():
     t2 = th.copy(); m = np.zeros_like(th); v = np.zeros_like(th)
     oracle.adam_step(t2, g, m, v, 1, lr=1e-3)
     assert np.allclose(t2, th - 1e-3 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+
+
+def test_dense_matvec_multi_equals_single():
+    # several force vectors share each pair block's evaluation but keep the
+    # single-vector summation order, so every product is bit-identical
+    X = hh_synth.rsa_cube(400, 0.1, seed=31)
+    k = oracle.PairKernel("mlp", hh_synth.mlp_params(32, 7), 32)
+    Fs = np.stack([hh_synth.forces(400, s) for s in range(5)])
+    rows = np.array([0, 7, 123, 399])
+    Um = oracle.dense_matvec_multi(X, Fs, k, rows=rows, with_self=False)
+    for f in range(5):
+        assert np.array_equal(Um[f], oracle.dense_matvec(X, Fs[f], k, rows=rows, with_self=False))
+    assert np.array_equal(oracle.dense_matvec_multi(X, Fs[:1], k)[0], oracle.dense_matvec(X, Fs[0], k))
