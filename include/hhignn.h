@@ -418,6 +418,26 @@ hh_status hh_filament_step(hh_ctx *ctx, double *X_dev, int64_t n_chains, int32_t
                            const hh_filament_params *fp, const hh_params *p, double dt, void *stream,
                            double *F_dev, double *U_dev);
 
+/* Test hooks for the failure paths (the paper has no counterpart).
+ *
+ * hh_debug_fail_alloc(n): the n-th device allocation made by the library
+ * from now on (n >= 1; process-wide) fails as if the pool were exhausted;
+ * the call that meets it returns HH_ERR_OOM after waiting for the device
+ * and freeing every temporary it had made, so the pool's used memory
+ * returns to its level before the call and the context stays usable.  n = 0
+ * cancels a pending failure.
+ *
+ * hh_debug_stall_mma_waits(ctx, polls): polls > 0 makes every MMA
+ * completion wait of this context's tensor-core kernels (HH_BF16) watch,
+ * for `polls` polls, an mbarrier that nothing arrives at instead of the
+ * MMA's own, so the wait runs out as it would for an MMA that never
+ * completed: the kernel records HH_ERR_TIMEOUT and abandons its work, and
+ * before it releases its accumulator memory it still waits, with the
+ * built-in limit (2^26 polls), for the MMA it issued.  polls = 0 restores
+ * normal waits.  Synchronises the device; HH_ERR_CUDA on a failed copy. */
+void hh_debug_fail_alloc(int64_t n);
+hh_status hh_debug_stall_mma_waits(hh_ctx *ctx, uint32_t polls);
+
 void hh_tree_free(hh_tree *t);
 void hh_blocks_free(hh_blocks *b);
 void hh_hmat_free(hh_hmat *h);

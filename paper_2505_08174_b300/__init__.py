@@ -36,6 +36,7 @@ EXPORTS = [
     "hh_aca_block_apply_noalloc", "hh_eval_pairs", "hh_train_loss_grad", "hh_train_step",
     "hh_set_launch", "hh_get_launch", "hh_autotune", "hh_set_short_range", "hh_short_range",
     "hh_filament_forces", "hh_filament_step", "hh_probe_throughput", "hh_shard_owners",
+    "hh_debug_fail_alloc", "hh_debug_stall_mma_waits",
 ]
 
 
@@ -114,6 +115,8 @@ def lib():
             "hh_export_factors": (st, [_P, _P, _P, _P, _P]),
             "hh_probe_throughput": (st, [_P, i32, ctypes.c_int64, _P, _P]),
             "hh_shard_owners": (st, [_P, i32, _P, _P]),
+            "hh_debug_fail_alloc": (None, [ctypes.c_int64]),
+            "hh_debug_stall_mma_waits": (st, [_P, ctypes.c_uint32]),
             "hh_stats": (st, [_P, _P]),
             "hh_tree_free": (None, [_P]),
             "hh_blocks_free": (None, [_P]),
@@ -141,6 +144,12 @@ def lib():
 
 FLAG_SHORT_RANGE = 1
 FLAG_PIVOTS_ONLY = 2
+
+
+def debug_fail_alloc(n: int):
+    """Test hook: the n-th device allocation of the library from now on fails
+    (HH_ERR_OOM, with the call's temporaries freed); 0 cancels."""
+    lib().hh_debug_fail_alloc(int(n))
 
 
 def Params(leaf_size=32, eta=1.0, eps=1e-4, max_rank=48, precision="fp32", kernel="mlp", radius=1.0,
@@ -323,6 +332,11 @@ class Context:
         self._check(lib().hh_probe_throughput(self._h, self.PROBES[kind], int(iters), _stream(stream),
                                               ctypes.byref(v)), "hh_probe_throughput")
         return v.value
+
+    def debug_stall_mma_waits(self, polls: int):
+        """Test hook: MMA completion waits watch a barrier nothing arrives at
+        for `polls` polls, so they run out (0: normal waits)."""
+        self._check(lib().hh_debug_stall_mma_waits(self._h, int(polls)), "hh_debug_stall_mma_waits")
 
     def stats(self) -> dict:
         s = CStats()

@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(128, 4) k_round_tiles(RoundArgs R, const float
     if (blockIdx.x >= n_groups && blockIdx.x * 4u >= n_plain) return;   // nothing for this CTA
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TileSmem<W>& sm = *reinterpret_cast<TileSmem<W>*>(smem_raw);
-    tc_setup<W>(sm.tc, th);
+    tc_setup<W>(sm.tc, th, R.status);
     uint32_t phase_bits = 0;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     float* const pv = sm.piv[warp];
@@ -952,19 +952,21 @@ void aca_rounds_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh
             if (pending) {
                 HH_CUDA(cudaEventSynchronize(ctx->poll_ev));
                 read_batch(set ^ 1);
-                if (h_cnt[0] == 0 && h_cnt[1] == 0) {
+                // done, or a bounded wait gave up (the caller reads the status)
+                if ((h_cnt[0] == 0 && h_cnt[1] == 0) || (h_cnt[2] & HH_DEV_TIMEOUT)) {
                     HH_CUDA(cudaEventSynchronize(rev.e[set][CHECK - 1][2]));
                     read_batch(set);
                     break;
                 }
             }
             HH_CUDA(cudaMemcpyAsync(h_cnt, cnt + 2 * (rr % 3), 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+            HH_CUDA(cudaMemcpyAsync(h_cnt + 2, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
             HH_CUDA(cudaEventRecord(ctx->poll_ev, s));
             pending = true;
             if (rr > limit) {
                 HH_CUDA(cudaEventSynchronize(ctx->poll_ev));
                 read_batch(set);
-                if (h_cnt[0] == 0 && h_cnt[1] == 0) break;
+                if ((h_cnt[0] == 0 && h_cnt[1] == 0) || (h_cnt[2] & HH_DEV_TIMEOUT)) break;
                 throw HHError{HH_ERR_CUDA, "ACA rounds did not finish within their bound"};
             }
         }

@@ -46,11 +46,14 @@ template <int W>
 __host__ __device__ constexpr uint32_t aca_tmem_cols() { return W <= 32 ? 128u : 256u; }
 
 template <int W, class S>
-__device__ void aca_tc_setup(S& sm, const float* th)
+__device__ void aca_tc_setup(S& sm, const float* th, const unsigned* status)
 {
     tc_load_weights<W>(sm.tc, th);
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         for (int w = 0; w < 4; ++w) { mbar_init(&sm.mbw[w], 1); sm.failw[w] = 0; }
+        sm.tc.stall_polls = tc_stall_polls(status);
+        mbar_init(&sm.tc.stall, 1);
+    }
     if (threadIdx.x < 32) {
         tmem_alloc(&sm.tc.tmem, aca_tmem_cols<W>());
         tmem_relinquish();
@@ -83,7 +86,7 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
     constexpr bool CTA = NT == 1;   // one 128-thread team per CTA, else 4 warp teams
     extern __shared__ __align__(128) unsigned char smem_raw[];
     AcaTcSmem<W, Team, MR>& S = *reinterpret_cast<AcaTcSmem<W, Team, MR>*>(smem_raw);
-    aca_tc_setup<W>(S, th_packed);
+    aca_tc_setup<W>(S, th_packed, A.status);
     const Team tm;
     const int team = threadIdx.x / SIZE;
     const int tid = tm.tid();
@@ -91,7 +94,8 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
     float* const ws = A.scratch + ((int64_t)blockIdx.x * NT + team) * A.team_stride;
     const float a = (float)A.pp.a;
     const int warp = threadIdx.x >> 5;   // TMEM quadrant, accumulator columns and mbarrier of this warp
-    TcWarp tw{S.tc.tmem + (uint32_t)(W * warp), &S.mbw[warp], 0u, &S.failw[warp], &S.pend[warp]};
+    TcWarp tw{S.tc.tmem + (uint32_t)(W * warp), &S.mbw[warp], 0u, &S.failw[warp], &S.pend[warp],
+              &S.tc.stall, S.tc.stall_polls};
 
     // state of the team's current block (uniform over the team; lam2 is
     // maintained by thread 0 only)

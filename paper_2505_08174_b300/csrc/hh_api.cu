@@ -85,17 +85,22 @@ __global__ void k_fill(double* __restrict__ a, int64_t n, double v)
     if (i < n) a[i] = v;
 }
 
+// Runs an entry point: its errors become a status and a message, and the
+// temporaries it had taken when it failed are freed.
 template <typename F>
 hh_status guarded(hh_ctx* ctx, F&& f)
 {
+    AllocScope scope;
     try {
         hh_status st = f();
         if (ctx) ctx->err.clear();
         return st;
     } catch (const HHError& e) {
+        scope.release();
         if (ctx) ctx->err = e.msg;
         return e.st;
     } catch (const std::bad_alloc&) {
+        scope.release();
         if (ctx) ctx->err = "host allocation failed";
         return HH_ERR_OOM;
     }
@@ -233,9 +238,9 @@ hh_status hh_create(hh_ctx** out, int device)
         HH_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
         uint64_t thr = UINT64_MAX;
         HH_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
-        HH_CUDA(cudaMalloc(&ctx->d_status, sizeof(unsigned)));
+        HH_CUDA(cudaMalloc(&ctx->d_status, 2 * sizeof(unsigned)));   // status bits, MMA-wait stall polls (test)
         HH_CUDA(cudaMalloc(&ctx->d_counters, 8 * sizeof(unsigned long long)));
-        HH_CUDA(cudaMemset(ctx->d_status, 0, sizeof(unsigned)));
+        HH_CUDA(cudaMemset(ctx->d_status, 0, 2 * sizeof(unsigned)));
         HH_CUDA(cudaMemset(ctx->d_counters, 0, 8 * sizeof(unsigned long long)));
         for (auto& e : ctx->ev) HH_CUDA(cudaEventCreate(&e));
         HH_CUDA(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
@@ -993,4 +998,14 @@ hh_status hh_filament_step(hh_ctx* ctx, double* X_dev, int64_t n_chains, int32_t
     });
     ctx->stats.n_launches = (int64_t)(g_hh_launches - base);
     return st2 != HH_OK ? st2 : st;
+}
+
+extern "C" hh_status hh_debug_stall_mma_waits(hh_ctx* ctx, uint32_t polls)
+{
+    if (!ctx) return HH_ERR_ARG;
+    return guarded(ctx, [&]() {
+        HH_CUDA(cudaDeviceSynchronize());
+        HH_CUDA(cudaMemcpy(ctx->d_status + 1, &polls, sizeof(unsigned), cudaMemcpyHostToDevice));
+        return HH_OK;
+    });
 }

@@ -113,6 +113,20 @@ void dev_radix_sort(uint64_t* keys, int32_t* vals, int64_t n, int key_bits, cuda
 // Stream-ordered allocation helpers.
 void* dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void* p, cudaStream_t s);
+// The temporaries (dev_alloc) an entry point takes while it runs: release()
+// frees those not freed yet, so a call that fails half-way leaks nothing.
+class AllocScope {
+public:
+    AllocScope();
+    ~AllocScope();
+    void release();
+    AllocScope(const AllocScope&) = delete;
+    AllocScope& operator=(const AllocScope&) = delete;
+
+private:
+    std::vector<std::pair<void*, cudaStream_t>> live_;
+    std::vector<std::pair<void*, cudaStream_t>>* prev_;
+};
 template <typename T>
 T* dev_alloc_t(int64_t n, cudaStream_t s) { return (T*)dev_alloc(sizeof(T) * (size_t)(n > 0 ? n : 1), s); }
 

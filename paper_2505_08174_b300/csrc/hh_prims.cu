@@ -1,23 +1,58 @@
 // hh_prims.cu -- device scan and stable LSD radix sort used by the tree,
 // the partition and the work lists.  256-thread CTAs, 2048 items per tile,
 // warp-synchronous stable ranking with __match_any_sync.
+
+#include <atomic>
 #include <utility>
+#include <vector>
 
 #include "hh_internal.h"
 
 unsigned long long g_hh_launches = 0;
 
+// Temporaries of the running call (see AllocScope) and the test hook that
+// makes an allocation fail.
+namespace {
+thread_local std::vector<std::pair<void*, cudaStream_t>>* g_live = nullptr;
+std::atomic<long long> g_fail_countdown{0};
+}  // namespace
+
 void* dev_alloc(size_t bytes, cudaStream_t s)
 {
+    long long c = g_fail_countdown.load();
+    while (c > 0 && !g_fail_countdown.compare_exchange_weak(c, c - 1)) {
+    }
+    if (c == 1) throw HHError{HH_ERR_OOM, "device allocation failed (injected by hh_debug_fail_alloc)"};
     void* p = nullptr;
     HH_CUDA(cudaMallocAsync(&p, bytes ? bytes : 16, s));
+    if (g_live) g_live->emplace_back(p, s);
     return p;
 }
 
 void dev_free(void* p, cudaStream_t s)
 {
-    if (p) HH_CUDA(cudaFreeAsync(p, s));
+    if (!p) return;
+    if (g_live)
+        for (auto it = g_live->rbegin(); it != g_live->rend(); ++it)
+            if (it->first == p) {
+                g_live->erase(std::next(it).base());
+                break;
+            }
+    HH_CUDA(cudaFreeAsync(p, s));
 }
+
+AllocScope::AllocScope() : prev_(g_live) { g_live = &live_; }
+AllocScope::~AllocScope() { g_live = prev_; }
+void AllocScope::release()
+{
+    // the failed call may have left kernels running on several streams: wait
+    // for all of them, then free newest first
+    (void)cudaDeviceSynchronize();
+    for (auto it = live_.rbegin(); it != live_.rend(); ++it) (void)cudaFreeAsync(it->first, it->second);
+    live_.clear();
+}
+
+extern "C" void hh_debug_fail_alloc(int64_t n) { g_fail_countdown.store(n > 0 ? n : 0); }
 
 // ---------------------------------------------------------------------------
 // Exclusive scan (int64)

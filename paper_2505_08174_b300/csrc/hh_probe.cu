@@ -92,6 +92,7 @@ float probe_ms(int64_t grid, int64_t iters, float* sink, cudaStream_t s, cudaEve
 extern "C" hh_status hh_probe_throughput(hh_ctx* ctx, int32_t kind, int64_t iters, void* stream, double* ops_per_s)
 {
     if (!ctx || !ops_per_s) return HH_ERR_ARG;
+    AllocScope scope;
     try {
         HH_REQUIRE(kind >= 0 && kind <= 5, HH_ERR_ARG, "probe kind must be in [0, 5]");
         HH_REQUIRE(iters >= 1 && iters <= ((int64_t)1 << 30), HH_ERR_ARG, "iters must be in [1, 2^30]");
@@ -115,6 +116,7 @@ extern "C" hh_status hh_probe_throughput(hh_ctx* ctx, int32_t kind, int64_t iter
         ctx->err.clear();
         return HH_OK;
     } catch (const HHError& e) {
+        scope.release();
         ctx->err = e.msg;
         return e.st;
     }

@@ -110,6 +110,7 @@ extern "C" hh_status hh_shard_owners(const hh_blocks* b, int32_t n_shards, int32
 {
     if (!b || !b->tree) return HH_ERR_ARG;
     hh_ctx* ctx = b->tree->ctx;
+    AllocScope scope;
     try {
         HH_REQUIRE(n_shards >= 1, HH_ERR_ARG, "n_shards must be >= 1");
         const hh_tree* t = b->tree;
@@ -130,6 +131,7 @@ extern "C" hh_status hh_shard_owners(const hh_blocks* b, int32_t n_shards, int32
         if (ctx) ctx->err.clear();
         return HH_OK;
     } catch (const HHError& e) {
+        scope.release();
         if (ctx) ctx->err = e.msg;
         return e.st;
     }

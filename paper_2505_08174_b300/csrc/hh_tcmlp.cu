@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(TC_T, 4) k_eval_pairs_tc(const double* __restr
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TcCore<W>& sm = *reinterpret_cast<TcCore<W>*>(smem_raw);
-    tc_setup<W>(sm, th);
+    tc_setup<W>(sm, th, status);
     uint32_t phase = 0;
     const int t = threadIdx.x;
     for (int64_t base = (int64_t)blockIdx.x * TC_T; base < n; base += (int64_t)gridDim.x * TC_T) {
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(TC_T, 4) k_near_tc(const float* __restrict__ X
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     NearSmem<W>& sm = *reinterpret_cast<NearSmem<W>*>(smem_raw);
-    tc_setup<W>(sm.tc, th);
+    tc_setup<W>(sm.tc, th, status);
     uint32_t phase = 0;
     const int t = threadIdx.x;
     unsigned long long pairs = 0;

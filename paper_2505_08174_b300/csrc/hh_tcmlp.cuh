@@ -41,7 +41,15 @@ struct alignas(128) TcCore {
     uint32_t tmem;
     int fail;
     uint32_t pending;
+    // Test mode (status[1] = stall_polls > 0, set by the host): every MMA
+    // completion wait watches `stall`, an mbarrier that nothing arrives at,
+    // for stall_polls polls instead of the MMA's own barrier, so it runs out
+    // and takes the timeout path.  The teardown wait is never redirected.
+    uint64_t stall;
+    uint32_t stall_polls;
 };
+
+__device__ __forceinline__ uint32_t tc_stall_polls(const unsigned* status) { return status ? status[1] : 0u; }
 
 template <int W>
 __host__ __device__ constexpr uint32_t tmem_cols() { return W <= 32 ? 32u : 64u; }
@@ -132,7 +140,8 @@ __device__ __forceinline__ void tc_write_features(TcCore<W>& sm, int t, const fl
 template <int W>
 __device__ __forceinline__ bool tc_wait(TcCore<W>& sm, uint32_t& phase, unsigned* status)
 {
-    const bool ok = mbar_wait_bounded(&sm.mbar, phase & 1u, TC_WAIT_LIMIT);
+    const bool ok = sm.stall_polls ? mbar_wait_bounded(&sm.stall, 0u, sm.stall_polls)
+                                   : mbar_wait_bounded(&sm.mbar, phase & 1u, TC_WAIT_LIMIT);
     const int any_fail = __syncthreads_or(!ok);
     if (any_fail) {
         if (threadIdx.x == 0) {
@@ -243,12 +252,14 @@ __device__ bool tc_mlp_tile(TcCore<W>& sm, uint32_t& phase, unsigned* status, fl
 }
 
 template <int W>
-__device__ void tc_setup(TcCore<W>& sm, const float* th)
+__device__ void tc_setup(TcCore<W>& sm, const float* th, const unsigned* status)
 {
     tc_load_weights<W>(sm, th);
     if (threadIdx.x == 0) {
         sm.fail = 0;
+        sm.stall_polls = tc_stall_polls(status);
         mbar_init(&sm.mbar, 1);
+        mbar_init(&sm.stall, 1);
     }
     if (threadIdx.x < 32) {
         tmem_alloc(&sm.tmem, tmem_cols<W>());
@@ -285,11 +296,14 @@ struct TcWarp {
     uint32_t phase;
     int* fail;         // shared: set on a timeout
     uint32_t* pending; // shared: phase still outstanding after a timeout
+    uint64_t* stall;   // the CTA's test-mode barrier (see TcCore::stall)
+    uint32_t stall_polls;
 };
 
 __device__ __forceinline__ bool tcw_wait(TcWarp& w, unsigned* status)
 {
-    const bool ok = mbar_wait_bounded(w.mbar, w.phase & 1u, TC_WAIT_LIMIT);
+    const bool ok = w.stall_polls ? mbar_wait_bounded(w.stall, 0u, w.stall_polls)
+                                  : mbar_wait_bounded(w.mbar, w.phase & 1u, TC_WAIT_LIMIT);
     if (__any_sync(0xffffffffu, !ok)) {
         if ((threadIdx.x & 31) == 0) {
             *w.fail = 1;
