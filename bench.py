@@ -45,7 +45,9 @@ partial velocities inside the timed step.
 
 --workload selects a further configuration, one line each (1 GPU):
   batch64      64 suspensions (cubes and Gaussian clouds) in one batched call
-  grad200k     forward U plus the adjoint (dL/dF, dL/dX, dL/dtheta), FP64
+  grad200k     N = 200k Gaussian drop: BF16 forward U plus the adjoint of
+               the FP32 H-matrix (dL/dF, dL/dX, dL/dtheta; near-field entries
+               FP32, admissible blocks FP64, every sum in a fixed order)
   cube10m      N = 10M uniform cube
   shortrange1m the headline with the short-range terms of Eq. 6 switched on
   train        Eq. 5 training steps of the pair MLP
@@ -55,6 +57,12 @@ partial velocities inside the timed step.
   c2sweep      N = 100k, C_leaf 64: MLP 4-64-64-64-6 and RPY x FP64 / FP32 /
                BF16 x eta in {0.7, 1, 1.5} x zeta in {1e-3, 1e-4, 1e-6}, one
                line per cell with its error on 256 exact dense rows
+  twodrop      Section 4.3's two sedimenting drops (2 x 523,305 lattice
+               particles, F = (0, 0, -1), dt 0.01, zeta 0.1, C_leaf 50):
+               explicit Euler steps through hh_simulate, optional dumps
+  filsphere    Section 4.3's filament suspension (5120 chains x 21 beads +
+               107,520 free particles; k_t 20, k_b 50, dt 0.002, zeta 0.02,
+               C_leaf 50), the same way
   peaks        throughput of the units the pair-kernel MLP leans on (MUFU
                ex2 / rcp / tanh, FP32 and FP64 FMA, the epilogue SiLU), with
                the SM clock sampled meanwhile
@@ -612,10 +620,11 @@ def run_workload(args):
         n = args.n if args.n != 1_000_000 else 200000
         X = hh_synth.gaussian_cloud(n, 30.0, seed=7)[0]
         F, W = hh_synth.forces(n, 1), hh_synth.forces(n, 2)
-        # forward U by the fused prediction; the adjoint rebuilds the FP64 factors along the pivots of a
-        # pivots-only H-matrix (no factor storage)
-        p = hh.Params(leaf_size=args.leaf, eps=args.eps, precision="fp64")
-        pp = hh.Params(leaf_size=args.leaf, eps=args.eps, precision="fp64", pivots_only=True)
+        # forward U by the fused BF16 prediction; the adjoint of the FP32 H-matrix on the same positions:
+        # its near-field entries in FP32, its admissible blocks along the pivots of an FP64 pivots-only
+        # re-approximation, their factors rebuilt in FP64 group by group within the memory budget
+        p = hh.Params(leaf_size=args.leaf, eps=args.eps, precision="bf16")
+        pp = hh.Params(leaf_size=args.leaf, eps=args.eps, precision="fp32", pivots_only=True)
         Xd, Fd, Wd = torch.as_tensor(X).cuda(), torch.as_tensor(F).cuda(), torch.as_tensor(W).cuda()
         U = torch.empty_like(Xd)
         gF = torch.empty_like(Xd)
@@ -631,7 +640,7 @@ def run_workload(args):
         total_ms, clocks, launches = _timed(ctx, step, args.steps, args.warmup, dev)
         line.update({"metric": "particle-gradients/sec: forward U and dL/dF, dL/dX, dL/dtheta of L = sum w.U",
                      "value": n * args.steps / (total_ms / 1e3), "unit": "particles/s",
-                     "ms_per_step": total_ms / args.steps, "dtype": "f64",
+                     "ms_per_step": total_ms / args.steps, "dtype": "bf16 forward, f32 near / f64 far adjoint",
                      "config": {"workload": f"gaussian_drop_N{n}_sigma30a", "n": n, "leaf_size": args.leaf,
                                 "eps": args.eps, "l2": "flushed between steps (256 MB write)"},
                      "gpu_launches": launches, "clocks": clocks})
@@ -729,6 +738,56 @@ def run_workload(args):
                      "rel_err_ci95": rel_err_ci95(Ud, Uh[rows] - a1 * Fh[rows]),
                      "gpu_launches": launches,
                      "clocks": clocks})
+    elif args.workload in ("twodrop", "filsphere"):
+        # Section 4.3's time-stepped runs: explicit Euler steps through hh_simulate (forces, prediction and
+        # update on the GPU; positions copied to the host every --dump-every steps, written as .npy files
+        # under --dump-dir)
+        if args.workload == "twodrop":
+            X = hh_synth.two_drops()
+            nch, beads, dt, eps = 0, 1, 0.01, 0.1
+            fil = hh.Filament(g=(0.0, 0.0, -1.0))
+            cfg = {"workload": "two_lattice_drops_2x523305_radius175_spacing3.5_centres_3R_apart",
+                   "forces": "gravity (0, 0, -1)"}
+        else:
+            X, r_in, r_out = hh_synth.filament_sphere()
+            nch, beads, dt, eps = 5120, 21, 0.002, 0.02
+            fil = hh.Filament(k_bond=20.0, l0=3.0, kappa=50.0, g=(0.0, 0.0, -1.0))
+            cfg = {"workload": "filament_sphere_5120x21_beads_rb3_plus_107520_free",
+                   "r_in": r_in, "r_out": r_out,
+                   "forces": "gravity + bonds (k_t 20, l0 3) + bending (k_b 50), on the GPU"}
+        n = len(X)
+        p = hh.Params(leaf_size=50, eps=eps, precision=args.precision)
+        Xd = torch.as_tensor(X).cuda()
+        if args.warmup > 0:
+            ctx.simulate(Xd, p, dt, args.warmup, n_chains=nch, beads=beads, fil=fil)
+        X0 = Xd.cpu().numpy()
+        torch.cuda.synchronize()
+        with ClockSampler(dev) as clk:
+            t0 = time.perf_counter()
+            dumps, ts = ctx.simulate(Xd, p, dt, args.steps, n_chains=nch, beads=beads, fil=fil,
+                                     dump_every=args.dump_every)
+            wall = time.perf_counter() - t0
+        if dumps is not None and args.dump_dir:
+            os.makedirs(args.dump_dir, exist_ok=True)
+            for i, d in enumerate(dumps):
+                np.save(os.path.join(args.dump_dir, f"{args.workload}_step{args.warmup + i * args.dump_every:05d}.npy"), d)
+        # accuracy of the step's velocities at the positions the timed run started from
+        Fh = np.empty_like(X0)
+        Fh[:nch * beads] = oracle.filament_forces(X0[:nch * beads], beads, fil.k_bond, fil.l0, fil.kappa,
+                                                  tuple(fil.g)) if nch else Fh[:0]
+        Fh[nch * beads:] = np.asarray(fil.g)
+        Uh = ctx.predict(torch.as_tensor(X0).cuda(), torch.as_tensor(Fh).cuda(), p).cpu().numpy()
+        rows = np.sort(np.random.default_rng(0).choice(n, 32, replace=False))
+        Ud = oracle.dense_matvec(X0, Fh, kern, rows=rows, with_self=False)
+        line.update({"metric": "particle-velocities/sec per explicit Euler step (forces + H-HIGNN prediction + "
+                               "position update)",
+                     "value": n * args.steps / (float(np.sum(ts)) / 1e3), "unit": "particle-velocities/s",
+                     "ms_per_step": float(np.mean(ts)), "ms_per_step_each": [float(v) for v in ts],
+                     "wall_s_with_dumps": wall, "dtype": args.precision,
+                     "config": dict(cfg, n=n, dt=dt, leaf_size=50, eps=eps, steps_before=args.warmup,
+                                    dump_every=args.dump_every),
+                     "rel_err": float(oracle.rel_error(Ud, Uh[rows] - a1 * Fh[rows])), "rel_err_rows": len(rows),
+                     "gpu_launches": None, "clocks": clk.summary()})
     print(json.dumps(line), flush=True)
 
 
@@ -753,11 +812,14 @@ def main():
                     help="memory budget of the BF16 ACA's active blocks in MB (0 = the library default)")
     ap.add_argument("--profile", action="store_true",
                     help="run the warm-up and timed predictions only and print their stage times (for ncu runs)")
+    ap.add_argument("--dump-every", type=int, default=0,
+                    help="twodrop / filsphere: copy the positions to the host every this many steps")
+    ap.add_argument("--dump-dir", default=None, help="twodrop / filsphere: write the position dumps here (.npy)")
     ap.add_argument("--clocks-csv", default=None,
                     help="keep the raw nvidia-smi clock samples of the timed region in this file")
     ap.add_argument("--workload", default="cube1m",
                     choices=["cube1m", "batch64", "grad200k", "cube10m", "shortrange1m", "train", "filament1m", "peaks",
-                             "c2sweep"],
+                             "c2sweep", "twodrop", "filsphere"],
                     help="cube1m is the headline; the others measure further configurations")
     args = ap.parse_args()
     if args.clocks_csv:

@@ -18,6 +18,16 @@ synthetic equivalents):
 * ``filaments``      -- straight bead chains at random orientation, placed
                         without overlap; ``perturb`` gives a displaced variant
                         (the bead forces belong to the time step, not here).
+* ``lattice_sphere`` -- the sites of a primitive cubic lattice (one at the
+                        centre) inside a ball, each moved by a small uniform
+                        jitter: the paper's suspension drop; ``two_drops``
+                        stacks two of them on the z axis.
+* ``lattice_cube`` / ``lattice_subset`` -- a perturbed n^3 lattice and seeded
+                        random subsets of its sites (fixed domain, varying
+                        concentration).
+* ``filament_sphere`` -- the paper's filament suspension: bead chains placed
+                        in an inner ball, free particles in the shell around
+                        it, centre distances >= a minimum gap.
 * ``forces``         -- i.i.d. N(0,1) force components.
 * ``mlp_params``     -- Xavier-uniform weights drawn from SplitMix64, zero
                         biases, every value rounded to bfloat16 so that the
@@ -31,7 +41,7 @@ import numpy as np
 
 __all__ = [
     "cube_side", "rsa_cube", "sigma_min", "gaussian_cloud", "filaments",
-    "perturb",
+    "perturb", "lattice_sphere", "two_drops", "lattice_cube", "lattice_subset", "filament_sphere",
     "forces", "splitmix64", "uniform01", "mlp_params", "mlp_param_count",
     "round_bf16", "GEOMETRY_SEED",
 ]
@@ -272,6 +282,138 @@ def filaments(n_chains: int, beads: int, bond: float = 2.2, a: float = 1.0, phi:
                 keep = np.setdiff1d(np.arange(placed), drop)
                 starts[:len(keep)], dirs[:len(keep)] = starts[keep], dirs[keep]
                 placed = len(keep)
+
+
+def lattice_sphere(radius: float, spacing: float = 3.5, center=(0.0, 0.0, 0.0), jitter: float = 0.2,
+                   seed: int = GEOMETRY_SEED) -> np.ndarray:
+    """Sites of a primitive cubic lattice of the given spacing, one of them at
+    the centre, with |site - centre| <= radius (selected before the jitter),
+    each then moved by an i.i.d. uniform [-jitter, jitter] offset per
+    component.  Rows in lattice order (x-major).  With jitter <=
+    (spacing - 2a) / (2 sqrt 3) no two spheres of radius a overlap.  The
+    paper's drop (radius 175, about 10% volume fraction) is spacing 3.5:
+    the 523,305 lattice points of a ball of radius 50 lattice units."""
+    m = int(radius // spacing) + 1
+    g = np.arange(-m, m + 1, dtype=np.float64) * spacing
+    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    P = P[np.einsum("ij,ij->i", P, P) <= radius * radius]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    P = P + rng.uniform(-jitter, jitter, size=P.shape)
+    return np.ascontiguousarray(P + np.asarray(center, dtype=np.float64))
+
+
+def two_drops(radius: float = 175.0, spacing: float = 3.5, separation: float = 3.0, jitter: float = 0.2,
+              seed: int = GEOMETRY_SEED) -> np.ndarray:
+    """Two equal lattice drops on the z axis, vertically aligned, centres
+    separation * radius apart (the upper, trailing drop first in the rows);
+    each from lattice_sphere with its own seed."""
+    up = lattice_sphere(radius, spacing, (0.0, 0.0, separation * radius), jitter, seed)
+    down = lattice_sphere(radius, spacing, (0.0, 0.0, 0.0), jitter, seed + 1)
+    return np.ascontiguousarray(np.concatenate([up, down]))
+
+
+def lattice_cube(n_side: int, spacing: float = 3.5, jitter: float = 0.2, seed: int = GEOMETRY_SEED) -> np.ndarray:
+    """n_side^3 sites of a primitive cubic lattice, origin at a corner, each
+    moved by a uniform [-jitter, jitter] offset per component."""
+    g = np.arange(n_side, dtype=np.float64) * spacing
+    P = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.ascontiguousarray(P + rng.uniform(-jitter, jitter, size=P.shape))
+
+
+def lattice_subset(n: int, n_side: int = 100, spacing: float = 3.5, jitter: float = 0.2, seed: int = GEOMETRY_SEED,
+                   subset_seed: int = 0) -> np.ndarray:
+    """n distinct sites drawn uniformly (seeded) from the perturbed
+    n_side^3 lattice of lattice_cube, in lattice order: the domain stays
+    fixed while the concentration grows with n."""
+    P = lattice_cube(n_side, spacing, jitter, seed)
+    rng = np.random.Generator(np.random.PCG64(subset_seed))
+    idx = np.sort(rng.choice(len(P), size=n, replace=False))
+    return np.ascontiguousarray(P[idx])
+
+
+def filament_sphere(n_fil: int = 5120, beads: int = 21, rb: float = 3.0, n_free: int = 107520,
+                    min_gap: float = 2.1, seed: int = GEOMETRY_SEED):
+    """The paper's filament suspension: straight chains of `beads` beads
+    spaced rb apart, random orientation, placed whole and one batch at a time
+    inside the inner ball R_in = (1/2)^(1/3) R_out, R_out = 4 * 10^(1/3) *
+    (beads - 1) * rb (a chain's midpoint uniform in the ball of radius
+    R_in - (beads - 1) rb / 2, so every bead is inside R_in); then n_free
+    particles uniform in the shell R_in <= |x| <= R_out.  Every centre
+    distance between different chains, or involving a free particle, is
+    >= min_gap (candidates are checked against everything placed before
+    and against the earlier candidates of their batch).  Rows: chain c at
+    c*beads .. c*beads + beads - 1 in order along the chain, then the free
+    particles.  Returns (X, R_in, R_out)."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    r_out = 4.0 * 10.0 ** (1.0 / 3.0) * (beads - 1) * rb
+    r_in = 0.5 ** (1.0 / 3.0) * r_out
+    half = 0.5 * (beads - 1) * rb
+    offs = (np.arange(beads) - 0.5 * (beads - 1)) * rb
+
+    def in_ball(m, rad):
+        v = rng.normal(size=(m, 3))
+        v /= np.linalg.norm(v, axis=1)[:, None]
+        return v * (rad * rng.uniform(0.0, 1.0, size=m) ** (1.0 / 3.0))[:, None]
+
+    chains = np.empty((0, beads, 3))
+    stall = 0
+    while len(chains) < n_fil:
+        m = 256
+        mid = in_ball(m, r_in - half)
+        d = rng.normal(size=(m, 3))
+        d /= np.linalg.norm(d, axis=1)[:, None]
+        C = mid[:, None, :] + offs[None, :, None] * d[:, None, :]
+        ok = np.ones(m, dtype=bool)
+        if len(chains):
+            dist, _ = cKDTree(chains.reshape(-1, 3)).query(C.reshape(-1, 3), k=1, distance_upper_bound=min_gap)
+            ok &= ~(dist.reshape(m, beads) < min_gap).any(1)
+        keep = []
+        for j in range(m):
+            if not ok[j]:
+                continue
+            if keep:
+                Q = C[keep].reshape(-1, 3)
+                dd = Q[:, None, :] - C[j][None, :, :]
+                if (np.einsum("ijk,ijk->ij", dd, dd) < min_gap * min_gap).any():
+                    continue
+            keep.append(j)
+            if len(chains) + len(keep) == n_fil:
+                break
+        stall = stall + 1 if not keep else 0
+        if stall > 50:
+            raise RuntimeError("filament placement stalled")
+        chains = np.concatenate([chains, C[keep]])
+    beadsX = chains.reshape(-1, 3)
+    tree_b = cKDTree(beadsX)
+    free = np.empty((0, 3))
+    stall = 0
+    while len(free) < n_free:
+        need = n_free - len(free)
+        m = int(need * 1.25) + 64
+        v = rng.normal(size=(m, 3))
+        v /= np.linalg.norm(v, axis=1)[:, None]
+        rad = (r_in ** 3 + rng.uniform(0.0, 1.0, size=m) * (r_out ** 3 - r_in ** 3)) ** (1.0 / 3.0)
+        cand = v * rad[:, None]
+        dist, _ = tree_b.query(cand, k=1, distance_upper_bound=min_gap)
+        cand = cand[~(dist < min_gap)]
+        if len(free) and len(cand):
+            dist, _ = cKDTree(free).query(cand, k=1, distance_upper_bound=min_gap)
+            cand = cand[~(dist < min_gap)]
+        if len(cand) > 1:
+            pairs = cKDTree(cand).query_pairs(min_gap, output_type="ndarray")
+            if len(pairs):
+                bad = np.zeros(len(cand), dtype=bool)
+                bad[np.maximum(pairs[:, 0], pairs[:, 1])] = True
+                cand = cand[~bad]
+        cand = cand[:need]
+        stall = stall + 1 if len(cand) == 0 else 0
+        if stall > 50:
+            raise RuntimeError("free-particle placement stalled")
+        free = np.concatenate([free, cand]) if len(free) else cand
+    return np.ascontiguousarray(np.concatenate([beadsX, free[:n_free]])), r_in, r_out
 
 
 def perturb(X: np.ndarray, scale: float, seed: int) -> np.ndarray:

@@ -226,22 +226,23 @@ hh_status hh_aca_block_apply_noalloc(hh_ctx *ctx, const double *Xt_dev, int32_t 
                                      const double *F_dev, const hh_params *p, void *stream, double *y_dev,
                                      int32_t *rank_dev);
 
-/* (With an H-matrix built under HH_FLAG_PIVOTS_ONLY, gF_dev too comes from
- * the FP64 factors rebuilt along the pivots, its admissible-block part summed
- * with FP64 atomics: equal to the transposed product up to summation order.)
- *
- * Adjoint of L = sum_i gU_i . U_i for U = alpha_1 F + M_H F built by hh_aca
+/* Adjoint of L = sum_i gU_i . U_i for U = alpha_1 F + M_H F built by hh_aca
  * with the MLP kernel (Section 3, Eqs. 4 and 8 differentiated; the paper
  * trains the MLP on pairs and has no H-matrix adjoint): gF_dev = alpha_1 gU
  * + M_H^T gU (FP64 [N,3]), gX_dev += dL/dX (FP64 [N,3]) and gtheta_dev +=
  * dL/dtheta (float32, length of theta), the last two with tree, partition
- * and ACA pivots frozen, evaluated in FP64.  For an FP32 or BF16 h, dL/dX and
- * dL/dtheta are those of the FP64 H-matrix on the same tree and partition
- * (its ACA, pivots only, is run inside the call): pivots picked from
- * low-precision residuals do not give a usable derivative of the rank
- * recursion.  Any of
- * gF_dev, gX_dev, gtheta_dev may be NULL; gX and gtheta are accumulated
- * into (zero them first).  Near-field activations are recomputed, not
+ * and ACA pivots frozen.  The admissible blocks are differentiated in FP64:
+ * for an FP32 or BF16 h, along the pivots of the FP64 H-matrix on the same
+ * tree and partition (its ACA, pivots only, is run inside the call; pivots
+ * picked from low-precision residuals do not give a usable derivative of
+ * the rank recursion).  The near-field entries are differentiated in the
+ * precision the product used for them (FP64 for an FP64 h, else FP32).
+ * When h holds pivots only, its FP64 factors are rebuilt group by group
+ * (hh_params.mem_budget bounds the groups' buffers), and gF_dev's
+ * admissible part comes from them: equal to the transposed product up to
+ * summation order.  Every sum has a fixed order: repeated calls give the
+ * same bits.  Any of gF_dev, gX_dev, gtheta_dev may be NULL; gX and gtheta
+ * are accumulated into (zero them first).  Activations are recomputed, not
  * stored. */
 hh_status hh_matvec_backward(hh_ctx *ctx, const hh_hmat *h, const double *gU_dev, const double *F_dev,
                              double *gF_dev, double *gX_dev, float *gtheta_dev, void *stream);
@@ -417,6 +418,25 @@ hh_status hh_filament_forces(hh_ctx *ctx, const double *X_dev, int64_t n_chains,
 hh_status hh_filament_step(hh_ctx *ctx, double *X_dev, int64_t n_chains, int32_t beads,
                            const hh_filament_params *fp, const hh_params *p, double dt, void *stream,
                            double *F_dev, double *U_dev);
+
+/* A run of explicit Euler steps of a suspension of chains and free
+ * particles (Section 2.5's time stepping; the drop and filament runs of
+ * Section 4.3), in place on X_dev ([N, 3] FP64 device, N = n_chains * beads
+ * + n_free): rows 0 .. n_chains * beads - 1 are chains as in
+ * hh_filament_forces, the remaining n_free rows free particles that feel
+ * fp->g only (a drop: n_chains = 0).  Each step k = 1 .. n_steps:
+ *   F = forces(X);  U = alpha_1 F + M_H(X) F (hh_predict under p);  X += dt U.
+ * With dump_every > 0, X_dump_host (host, caller-owned, FP64
+ * [n_steps / dump_every + 1, N, 3]) receives the initial X in slot 0 and X
+ * after step k in slot k / dump_every for every k divisible by dump_every.
+ * t_step_ms (host, [n_steps], may be NULL) receives each step's device time
+ * (CUDA events: forces through update).  Errors as hh_filament_step; an
+ * error stops the run with X after the last completed step (the dumps up
+ * to it written).  HH_WARN_RANK_CAP from any step is returned at the end.
+ * Synchronises the device's work on stream before it returns. */
+hh_status hh_simulate(hh_ctx *ctx, double *X_dev, int64_t n_chains, int32_t beads, int64_t n_free,
+                      const hh_filament_params *fp, const hh_params *p, double dt, int32_t n_steps,
+                      int32_t dump_every, double *X_dump_host, double *t_step_ms, void *stream);
 
 /* Test hooks for the failure paths (the paper has no counterpart).
  *

@@ -385,3 +385,24 @@ def euler_step(X, beads, kernel, dt, leaf=32, eta=1.0, eps=1e-4, max_rank=48, k=
     F = filament_forces(X, beads, k, l0, kappa, g)
     U, _ = hmatvec(X, F, kernel, leaf=leaf, eta=eta, eps=eps, max_rank=max_rank)
     return X + dt * U, F, U
+
+
+def simulate(X, n_chains, beads, kernel, dt, n_steps, dump_every=1, leaf=32, eta=1.0, eps=1e-4, max_rank=48,
+             k=100.0, l0=2.2, kappa=10.0, g=(0.0, 0.0, -1.0)):
+    """n_steps explicit Euler steps (Section 2.5) of chains (the first
+    n_chains * beads rows, forces of filament_forces) and free particles (the
+    remaining rows, force g): F = F(X), U = alpha_1 F + M_H F (hmatvec),
+    X <- X + dt U.  Returns the list of X at step 0 and at every step
+    divisible by dump_every."""
+    X = _f64(X).copy()
+    nc = n_chains * beads
+    dumps = [X.copy()]
+    for step in range(1, n_steps + 1):
+        F = np.empty_like(X)
+        F[:nc] = filament_forces(X[:nc], beads, k, l0, kappa, g) if nc else F[:0]
+        F[nc:] = np.asarray(g, dtype=np.float64)
+        U, _ = hmatvec(X, F, kernel, leaf=leaf, eta=eta, eps=eps, max_rank=max_rank)
+        X = X + dt * U
+        if dump_every and step % dump_every == 0:
+            dumps.append(X.copy())
+    return dumps

@@ -36,7 +36,7 @@ EXPORTS = [
     "hh_aca_block_apply_noalloc", "hh_eval_pairs", "hh_train_loss_grad", "hh_train_step",
     "hh_set_launch", "hh_get_launch", "hh_autotune", "hh_set_short_range", "hh_short_range",
     "hh_filament_forces", "hh_filament_step", "hh_probe_throughput", "hh_shard_owners",
-    "hh_debug_fail_alloc", "hh_debug_stall_mma_waits",
+    "hh_debug_fail_alloc", "hh_debug_stall_mma_waits", "hh_simulate",
 ]
 
 
@@ -116,6 +116,8 @@ def lib():
             "hh_probe_throughput": (st, [_P, i32, ctypes.c_int64, _P, _P]),
             "hh_shard_owners": (st, [_P, i32, _P, _P]),
             "hh_debug_fail_alloc": (None, [ctypes.c_int64]),
+            "hh_simulate": (st, [_P, _P, ctypes.c_int64, i32, ctypes.c_int64, _P, _P, ctypes.c_double, i32, i32, _P,
+                                 _P, _P]),
             "hh_debug_stall_mma_waits": (st, [_P, ctypes.c_uint32]),
             "hh_stats": (st, [_P, _P]),
             "hh_tree_free": (None, [_P]),
@@ -304,6 +306,26 @@ class Context:
                                     ctypes.byref(params), float(dt), _stream(stream), _dptr(F), _dptr(U))
         self.last_status = self._check(st, "hh_filament_step")
         return F, U
+
+    def simulate(self, X, params: CParams, dt, n_steps, n_chains=0, beads=1, fil: CFilament = None, dump_every=0,
+                 stream=None):
+        """n_steps explicit Euler steps in place on X (chains first, then free
+        particles feeling g only; see hh_simulate).  Returns (dumps, t_step_ms):
+        dumps [n_steps // dump_every + 1, N, 3] float64 (None when dump_every
+        is 0), t_step_ms [n_steps]."""
+        _check_xyz(X, "X")
+        n_free = X.shape[0] - n_chains * beads
+        if n_chains < 0 or beads < 1 or n_free < 0:
+            raise ValueError("X must hold n_chains chains of `beads` rows, then the free particles")
+        fil = Filament() if fil is None else fil
+        dumps = np.zeros((n_steps // dump_every + 1, X.shape[0], 3)) if dump_every > 0 else None
+        ts = np.zeros(max(n_steps, 1))
+        st = lib().hh_simulate(self._h, _dptr(X), int(n_chains), int(beads), int(n_free), ctypes.byref(fil),
+                               ctypes.byref(params), float(dt), int(n_steps), int(dump_every),
+                               dumps.ctypes.data_as(_P) if dumps is not None else None, ts.ctypes.data_as(_P),
+                               _stream(stream))
+        self.last_status = self._check(st, "hh_simulate")
+        return dumps, ts[:n_steps]
 
     # -- launch shape and autotuner ---------------------------------------------
     def set_launch(self, small_max=0, aca_small_cps=0, aca_large_cps=0, near_cps=0, rounds_min_cq=0):

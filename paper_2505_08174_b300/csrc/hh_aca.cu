@@ -249,7 +249,7 @@ __device__ void aca_block(const AcaArgs<R>& A, const Team& tm, S& sm, const R* t
             out[3 * m] = y0; out[3 * m + 1] = y1; out[3 * m + 2] = y2;
         }
     } else if (mode == 2) {
-        R* dst = A.fac + 9 * A.fofs[b];
+        R* dst = A.fac + 9 * (A.fofs[b] - A.fofs_base);
         const int64_t nc = (int64_t)l * 9 * c, nq = (int64_t)l * 9 * q;
         for (int64_t x = tid; x < nc; x += SIZE) dst[x] = Cs[x];
         for (int64_t x = tid; x < nq; x += SIZE) dst[nc + x] = Qs[x];

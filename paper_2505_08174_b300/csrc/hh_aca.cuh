@@ -40,6 +40,7 @@ struct AcaArgs {
     int64_t pofs_base;     // block b's partial output at part + 3 * (pofs[b] - pofs_base)
     R* fac;
     const int64_t* fofs;
+    int64_t fofs_base;
     unsigned* status;
     unsigned long long* n_queries;
 };
@@ -263,6 +264,7 @@ AcaArgs<R> make_aca_args(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, con
     A.pofs_base = r.pofs_base;
     A.fac = (R*)r.factors;
     A.fofs = r.fofs;
+    A.fofs_base = r.fofs_base;
     A.status = ctx->d_status;
     A.n_queries = ctx->d_counters + 4;
     return A;

@@ -111,6 +111,7 @@ struct RoundArgs {
     int64_t pofs_base;         // block b's partial output at part + 3 * (pofs[b] - pofs_base)
     float* fac;
     const int64_t* fofs;
+    int64_t fofs_base;
     unsigned* status;
     unsigned long long* n_queries;
 };
@@ -379,7 +380,7 @@ __device__ __forceinline__ void plain_seg(const RoundArgs& R, const SegView& g, 
         // the room the first (pivots-only) pass sized for this block
         const int64_t cap = (R.fofs[g.b + 1] - R.fofs[g.b]) / (int64_t)(c + q);
         if (l <= cap) {
-            float* dst = R.fac + 9 * R.fofs[g.b];
+            float* dst = R.fac + 9 * (R.fofs[g.b] - R.fofs_base);
             if (x < c)
                 for (int pe = 0; pe < 9 * l; ++pe) dst[(int64_t)pe * c + x] = Cs[(int64_t)pe * c + x];
             if (x < q)
@@ -847,6 +848,7 @@ void aca_rounds_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh
     R.pofs_base = r.pofs_base;
     R.fac = (float*)r.factors;
     R.fofs = r.fofs;
+    R.fofs_base = r.fofs_base;
     R.status = base.status;
     R.n_queries = base.n_queries;
 

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
                 out[3 * m] = y0; out[3 * m + 1] = y1; out[3 * m + 2] = y2;
             }
         } else if (mode == 2) {
-            float* dst = A.fac + 9 * A.fofs[b];
+            float* dst = A.fac + 9 * (A.fofs[b] - A.fofs_base);
             const int64_t nc = (int64_t)l * 9 * c, nq = (int64_t)l * 9 * q;
             for (int64_t x = tid; x < nc; x += SIZE) dst[x] = Cs[x];
             for (int64_t x = tid; x < nq; x += SIZE) dst[nc + x] = Qs[x];

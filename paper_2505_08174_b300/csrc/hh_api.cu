@@ -677,7 +677,7 @@ hh_status hh_matvec_backward(hh_ctx* ctx, const hh_hmat* h, const double* gU_dev
             gFs = dev_alloc_t<double>(3 * t->n, s);
             HH_CUDA(cudaMemsetAsync(gFs, 0, sizeof(double) * 3 * t->n, s));
         }
-        matvec_backward_xtheta(ctx, hx, Fs, Ws, gX_dev, gtheta_dev, gFs, s);
+        matvec_backward_xtheta(ctx, hx, h->params.precision != HH_FP64, Fs, Ws, gX_dev, gtheta_dev, gFs, s);
         if (gF_here) {
             // near part (transposed, FP64) and alpha_1 w, then caller order
             const hh_params& px = hx->params;
@@ -998,6 +998,74 @@ hh_status hh_filament_step(hh_ctx* ctx, double* X_dev, int64_t n_chains, int32_t
     });
     ctx->stats.n_launches = (int64_t)(g_hh_launches - base);
     return st2 != HH_OK ? st2 : st;
+}
+
+hh_status hh_simulate(hh_ctx* ctx, double* X_dev, int64_t n_chains, int32_t beads, int64_t n_free,
+                      const hh_filament_params* fp, const hh_params* p, double dt, int32_t n_steps,
+                      int32_t dump_every, double* X_dump_host, double* t_step_ms, void* stream)
+{
+    if (!ctx) return HH_ERR_ARG;
+    double* F = nullptr;
+    double* U = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int64_t n = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    FilamentArgs a{};
+    // checks and the per-run buffers
+    hh_status st = guarded(ctx, [&]() {
+        check_chains(n_chains, beads);
+        HH_REQUIRE(n_free >= 0 && n_free < (1LL << 30), HH_ERR_ARG, "n_free must be in [0, 2^30)");
+        n = n_chains * beads + n_free;
+        HH_REQUIRE(n >= 1 && n < (1LL << 30), HH_ERR_ARG, "need 1 <= n_chains * beads + n_free < 2^30");
+        a = filament_args(fp);
+        check_params(ctx, p);
+        HH_REQUIRE(std::isfinite(dt), HH_ERR_ARG, "dt must be finite");
+        HH_REQUIRE(n_steps >= 0 && dump_every >= 0, HH_ERR_ARG, "n_steps and dump_every must be >= 0");
+        HH_REQUIRE(X_dev != nullptr && (dump_every == 0 || X_dump_host != nullptr), HH_ERR_ARG, "NULL argument");
+        HH_CUDA(cudaMalloc(&F, sizeof(double) * 3 * n));
+        HH_CUDA(cudaMalloc(&U, sizeof(double) * 3 * n));
+        HH_CUDA(cudaEventCreate(&ev[0]));
+        HH_CUDA(cudaEventCreate(&ev[1]));
+        if (dump_every > 0)
+            HH_CUDA(cudaMemcpyAsync(X_dump_host, X_dev, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+        return HH_OK;
+    });
+    const int64_t offsets[2] = {0, n};
+    hh_status worst = HH_OK;
+    for (int32_t k = 1; st == HH_OK && k <= n_steps; ++k) {
+        st = guarded(ctx, [&]() {
+            reset_call(ctx, s);
+            HH_CUDA(cudaEventRecord(ev[0], s));
+            const int64_t nc = n_chains * beads;
+            if (n_chains > 0) filament_forces_launch(ctx, X_dev, n_chains, beads, a, F, s);
+            if (n_free > 0) filament_forces_launch(ctx, X_dev + 3 * nc, n_free, 1, a, F + 3 * nc, s);   // g only
+            return read_status(ctx, s);
+        });
+        if (st != HH_OK) break;
+        hh_status sp = hh_predict(ctx, X_dev, F, offsets, 1, p, stream, U);
+        if (sp != HH_OK && sp != HH_WARN_RANK_CAP) { st = sp; break; }
+        if (sp == HH_WARN_RANK_CAP) worst = sp;
+        st = guarded(ctx, [&]() {
+            euler_launch(X_dev, U, 3 * n, dt, s);
+            HH_CUDA(cudaEventRecord(ev[1], s));
+            if (dump_every > 0 && k % dump_every == 0)
+                HH_CUDA(cudaMemcpyAsync(X_dump_host + (int64_t)(k / dump_every) * 3 * n, X_dev,
+                                        sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+            HH_CUDA(cudaEventSynchronize(ev[1]));
+            if (t_step_ms) {
+                float ms = 0.f;
+                HH_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+                t_step_ms[k - 1] = ms;
+            }
+            return HH_OK;
+        });
+    }
+    if (st == HH_OK && stream != nullptr) (void)cudaStreamSynchronize(s);
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+    if (F) cudaFree(F);
+    if (U) cudaFree(U);
+    return st != HH_OK ? st : worst;
 }
 
 extern "C" hh_status hh_debug_stall_mma_waits(hh_ctx* ctx, uint32_t polls)

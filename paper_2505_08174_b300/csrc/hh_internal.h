@@ -168,8 +168,9 @@ struct AcaRun {
     int32_t* rank = nullptr;
     int32_t* pivI = nullptr;
     int32_t* pivJ = nullptr;
-    void* factors = nullptr;
+    void* factors = nullptr;       // mode 2: block b at 9 * (fofs[b] - fofs_base)
     const int64_t* fofs = nullptr;
+    int64_t fofs_base = 0;
     int mode = 0;
 };
 void aca_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* b, const hh_params& p, const AcaRun& r,
@@ -233,11 +234,13 @@ void short_range_add(hh_ctx* ctx, const double* X, const double* F, int64_t n, c
                      const int64_t* d_offsets, const hh_params& p, void* y, int y_double, cudaStream_t s);
 
 // Adjoint: dL/dX (added to gX, caller order) and dL/dtheta (added to gtheta)
-// of L = sum w . (M_H F) with frozen pivots (hh_backward.cu); Fs, Ws sorted.
-// gFs (sorted order, may be NULL) += the admissible blocks' part of M_H^T w
-// (FP64 atomics), from the same pass.
-void matvec_backward_xtheta(hh_ctx* ctx, const hh_hmat* h, const double* Fs, const double* Ws, double* gX,
-                            float* gtheta, double* gFs, cudaStream_t s);
+// of L = sum w . (M_H F) with frozen pivots (hh_backward.cu); Fs, Ws sorted;
+// h holds FP64 factors or pivots only.  The near-field entries run in FP32
+// when near_fp32 (the product's near field was FP32 or BF16), else FP64.
+// gFs (sorted order, may be NULL) += the admissible blocks' part of M_H^T w,
+// from the same pass.  Every sum has a fixed order (reproducible bit for bit).
+void matvec_backward_xtheta(hh_ctx* ctx, const hh_hmat* h, bool near_fp32, const double* Fs, const double* Ws,
+                            double* gX, float* gtheta, double* gFs, cudaStream_t s);
 
 // Training of the pair MLP (hh_train.cu).
 double train_loss_grad(hh_ctx* ctx, const float* theta, int width, const double* r, const double* e, const double* U,

@@ -146,11 +146,13 @@ def test_near_only_is_exact_dense_gradient(ctx):
     X = hh_synth.rsa_cube(n, 0.1, seed=45)
     F, W = hh_synth.forces(n, 9), hh_synth.forces(n, 10)
     gFo, gXo, gTo = oracle.dense_grad(X, F, W, oracle.PairKernel("mlp", THETA, 32))
-    for prec in ("fp64", "fp32"):
+    # FP64 H-matrix: FP64 entries (float32 theta output); FP32: the near
+    # field's entries run in FP32, as its product did
+    for prec, tx, tt in (("fp64", 1e-12, 1e-6), ("fp32", 2e-5, 2e-5)):
         gF, gX, gT, (t, b, h) = grads(ctx, X, F, W, hh.Params(precision=prec, eta=1e-9))
         assert len(b.export()[0]) == 0
-        assert np.abs(gX - gXo).max() <= 1e-12 * np.abs(gXo).max()
-        assert np.abs(gT - gTo).max() <= 1e-6 * np.abs(gTo).max()    # float32 output
+        assert np.abs(gX - gXo).max() <= tx * np.abs(gXo).max(), prec
+        assert np.abs(gT - gTo).max() <= tt * np.abs(gTo).max(), prec
 
 
 def test_width64_gradient():
@@ -184,10 +186,10 @@ def test_autograd_function_matches_direct_calls(ctx):
     L = (U * cuda(W)).sum()
     L.backward()
     gF, gX, gT, _ = grads(ctx, X0, F0, W, p)
-    assert np.array_equal(F.grad.cpu().numpy(), gF)       # the transposed product is deterministic
-    # dL/dX and dL/dtheta are summed with FP64 atomics: equal up to summation order
-    assert np.abs(X.grad.cpu().numpy() - gX).max() <= 1e-12 * np.abs(gX).max()
-    assert np.abs(th.grad.cpu().numpy().astype(np.float64) - gT).max() <= 1e-6 * np.abs(gT).max()
+    # every sum of the adjoint has a fixed order: the same bits either way
+    assert np.array_equal(F.grad.cpu().numpy(), gF)
+    assert np.array_equal(X.grad.cpu().numpy(), gX)
+    assert np.array_equal(th.grad.cpu().numpy().astype(np.float64), gT)
     Ud, _ = loss(ctx, X0, F0, W, p)
     assert float(L.detach()) == pytest.approx(Ud, rel=1e-14)
 
@@ -211,3 +213,59 @@ def test_pivots_only_hmatrix_gives_the_same_gradients(ctx):
     assert np.abs(gF2.cpu().numpy() - gF).max() <= 1e-12 * np.abs(gF).max()
     assert np.abs(gX2.cpu().numpy() - gX).max() <= 1e-10 * np.abs(gX).max()
     assert np.abs(gT2.cpu().numpy() - gT).max() <= 1e-5 * np.abs(gT).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_gradients_are_reproducible_and_budget_independent(ctx, prec):
+    # fixed summation orders: a second call gives the same bits; a small
+    # memory budget splits the admissible blocks into groups, which changes
+    # only the order of the FP64 sums (within rounding)
+    n = 6000
+    X = hh_synth.gaussian_cloud(n, 30.0, seed=49)[0]
+    F, W = hh_synth.forces(n, 17), hh_synth.forces(n, 18)
+    p = hh.Params(precision=prec, leaf_size=32, pivots_only=True)
+    gF1, gX1, gT1, _ = grads(ctx, X, F, W, p)
+    gF2, gX2, gT2, _ = grads(ctx, X, F, W, p)
+    assert np.array_equal(gF1, gF2) and np.array_equal(gX1, gX2) and np.array_equal(gT1, gT2)
+    pb = hh.Params(precision=prec, leaf_size=32, pivots_only=True, mem_budget=8 << 20)
+    gF3, gX3, gT3, _ = grads(ctx, X, F, W, pb)
+    assert np.abs(gF3 - gF1).max() <= 1e-12 * np.abs(gF1).max()
+    assert np.abs(gX3 - gX1).max() <= 1e-11 * np.abs(gX1).max()
+    assert np.abs(gT3 - gT1).max() <= 1e-6 * np.abs(gT1).max()
+
+
+def _golden_drop20k():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "grad_drop20k.txt")
+    with open(path) as f:
+        lines = [l for l in f if not l.startswith("#")]
+    nt = int(lines[0].split()[1])
+    gT = np.array([float(v) for v in lines[1:1 + nt]])
+    nr = int(lines[1 + nt].split()[1])
+    rows = np.array([[float(v) for v in l.split()] for l in lines[2 + nt:2 + nt + nr]])
+    return gT, rows[:, 0].astype(np.int64), rows[:, 1:4], rows[:, 4:7]
+
+
+def test_gradient_of_the_20k_drop_against_the_dense_oracle():
+    # the differentiation workload at N = 20,000 (Gaussian drop, sigma = 30 a):
+    # dL/dtheta in full and dL/dX, dL/dF on 128 rows against the FP64 dense
+    # gradient over all pairs (tests/golden/make_grad_drop20k.py).  The
+    # H-matrix gradient differs from the dense one by the ACA truncation:
+    # about zeta in relative norm (measured: see the tolerances)
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "make_grad_drop20k", os.path.join(os.path.dirname(__file__), "golden", "make_grad_drop20k.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    X, F, W, rows, _ = mk.inputs()
+    gTo, ro, gXo, gFo = _golden_drop20k()
+    assert np.array_equal(ro, rows)
+    c = hh.Context()
+    c.set_mlp(THETA, 32)
+    for prec, eps, tol in (("fp64", 1e-6, 1e-4), ("fp32", 1e-4, 3e-3)):
+        p = hh.Params(precision=prec, eps=eps, leaf_size=64, pivots_only=True)
+        gF, gX, gT, _ = grads(c, X, F, W, p)
+        assert np.linalg.norm(gT - gTo) <= tol * np.linalg.norm(gTo), prec
+        assert np.linalg.norm(gX[rows] - gXo) <= tol * np.linalg.norm(gXo), prec
+        assert np.linalg.norm(gF[rows] - gFo) <= tol * np.linalg.norm(gFo), prec

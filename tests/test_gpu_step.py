@@ -89,3 +89,61 @@ def test_step_is_forces_then_predict_then_update(ctx):
     # a second step starts from the moved positions
     F2, _ = ctx.filament_step(Xd, beads, p, dt)
     assert not torch.equal(F2, F)
+
+
+def _mixture(seed):
+    # a small version of the paper's filament suspension: chains inside, free
+    # particles in the shell around them
+    X, _, _ = hh_synth.filament_sphere(8, 6, 3.0, 300, seed=seed)
+    return X
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-6), ("bf16", 1e-4)])
+def test_simulate_against_oracle(ctx, prec, tol):
+    # hh_simulate: chains (bonds, bending, gravity) then free particles (gravity
+    # only); three steps with a dump after each, against the oracle's steps.
+    # Positions drift apart by at most dt * (the per-step velocity error),
+    # accumulated over the steps
+    X = _mixture(71)
+    fil = hh.Filament(k_bond=20.0, l0=3.0, kappa=50.0)
+    dt, steps = 0.05, 3
+    k = oracle.PairKernel("mlp", THETA, 32)
+    ref = oracle.simulate(X, 8, 6, k, dt, steps, dump_every=1, leaf=32, eps=1e-4, k=20.0, l0=3.0, kappa=50.0)
+    Xd = cuda(X)
+    dumps, ts = ctx.simulate(Xd, hh.Params(precision=prec, leaf_size=32), dt, steps, n_chains=8, beads=6, fil=fil,
+                             dump_every=1)
+    assert dumps.shape == (steps + 1, len(X), 3) and len(ts) == steps and np.all(ts > 0)
+    assert np.array_equal(dumps[0], X)
+    assert np.array_equal(dumps[-1], Xd.cpu().numpy())
+    for s in range(1, steps + 1):
+        Uo = (ref[s] - ref[s - 1]) / dt
+        assert np.max(np.abs(dumps[s] - ref[s])) <= s * dt * tol * np.abs(Uo).max() * np.sqrt(len(X)), s
+
+
+def test_simulate_is_repeated_steps(ctx):
+    # chains only: the same kernels as hh_filament_step, step after step
+    beads, dt = 21, 0.002
+    X = chains(60, beads, seed=81, scale=0.05)
+    p = hh.Params(precision="bf16", leaf_size=64)
+    Xa, Xb = cuda(X), cuda(X)
+    for _ in range(3):
+        ctx.filament_step(Xa, beads, p, dt)
+    dumps, _ = ctx.simulate(Xb, p, dt, 3, n_chains=60, beads=beads, dump_every=3)
+    assert torch.equal(Xa, Xb) and np.array_equal(dumps[1], Xb.cpu().numpy())
+    # a drop (free particles only) under gravity with the RPY kernel: every
+    # pair term pulls along the force (both RPY coefficients are positive for
+    # r >= 2a), so every particle sinks, and faster than alone
+    D0 = hh_synth.lattice_sphere(20.0, 3.5)
+    D = cuda(D0)
+    ctx.simulate(D, hh.Params(precision="fp64", kernel="rpy", leaf_size=64), 0.5, 2)
+    dz = D.cpu().numpy()[:, 2] - D0[:, 2]
+    assert np.all(dz < 2 * 0.5 * -oracle.self_mobility())
+
+
+def test_simulate_stops_at_an_error(ctx):
+    X = np.array([[1.0, 2.0, 3.0], [1.0, 2.0, 3.0], [3.2, 2.0, 3.0], [9.0, 9.0, 9.0]])
+    Xd = cuda(X)
+    with pytest.raises(hh.HHError) as e:
+        ctx.simulate(Xd, hh.Params(precision="fp64"), 0.01, 2, n_chains=1, beads=3, dump_every=1)
+    assert e.value.status == hh.HH_ERR_NUMERIC
+    assert np.array_equal(Xd.cpu().numpy(), X)

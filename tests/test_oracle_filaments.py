@@ -111,3 +111,33 @@ def test_euler_step_composes_its_parts():
     Ud = oracle.dense_matvec(X, F, k)                       # nothing admissible at 48 beads: exact
     assert oracle.rel_error(Ud, U) < 1e-13
     assert np.allclose(X1, X + 0.01 * U, rtol=0, atol=1e-15)
+
+
+def test_two_spheres_sediment_together_rpy_closed_form():
+    # Stokes flow: two identical spheres under the same force keep their
+    # relative position (the RPY pair tensor is even in r), and fall with
+    # U = F / (6 pi mu a) + K_RPY(r) F; for r along the force,
+    # K_RPY(r) F = F (1 + 2a^2/(3r^2) + 1 - 2a^2/r^2) / (8 pi mu r)
+    k = oracle.PairKernel("rpy")
+    r, dt = 5.0, 0.7
+    X0 = np.array([[0.3, -0.2, 1.0], [0.3, -0.2, 1.0 + r]])
+    dumps = oracle.simulate(X0, 0, 1, k, dt, 4, dump_every=1, leaf=8)
+    assert len(dumps) == 5
+    for Xk in dumps:
+        assert np.allclose(Xk[1] - Xk[0], [0, 0, r], rtol=0, atol=1e-13)
+    uz = -(1.0 / (6 * np.pi) + (2.0 + 2.0 / (3 * r * r) - 2.0 / (r * r)) / (8 * np.pi * r))
+    assert np.allclose(dumps[1] - dumps[0], [[0, 0, dt * uz]] * 2, rtol=1e-13, atol=0)
+    assert np.allclose(dumps[4] - dumps[0], [[0, 0, 4 * dt * uz]] * 2, rtol=1e-12, atol=0)
+
+
+def test_simulate_dt_zero_and_dump_slots():
+    k = oracle.PairKernel("mlp", hh_synth.mlp_params(32, 7), 32)
+    X, _, _ = hh_synth.filaments(3, 4, seed=8)
+    X = np.concatenate([hh_synth.perturb(X, 0.1, 9), hh_synth.rsa_cube(20, 0.1, seed=10) + 40.0])
+    d0 = oracle.simulate(X, 3, 4, k, 0.0, 3, dump_every=1)
+    assert all(np.array_equal(d, X) for d in d0)
+    d = oracle.simulate(X, 3, 4, k, 0.01, 5, dump_every=2)
+    assert len(d) == 3 and not np.array_equal(d[1], X)
+    Xe, _, _ = oracle.euler_step(X[:12], 4, k, 0.01)                 # chains alone: the one-step composition
+    de = oracle.simulate(X[:12], 3, 4, k, 0.01, 1)
+    assert np.array_equal(de[1], Xe)

@@ -93,3 +93,50 @@ def test_forces_and_perturb():
     X = np.zeros((1000, 3))
     P = hh_synth.perturb(X, 0.05, seed=1)
     assert abs(P.std() - 0.05) < 0.005 and np.array_equal(P, hh_synth.perturb(X, 0.05, seed=1))
+
+
+def test_lattice_drop_has_the_papers_particle_count():
+    # Section 4.3: each drop is the primitive cubic lattice inside a sphere of
+    # radius 175 at ~10% volume fraction, 523,305 particles (two drops:
+    # 1,046,610).  Spacing 3.5 gives exactly that count: the integer points
+    # of a ball of radius 50 lattice units.
+    P = hh_synth.lattice_sphere(175.0, 3.5)
+    assert len(P) == 523305
+    m = np.arange(-50, 51)
+    assert int(np.sum((m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2) <= 2500)) == 523305
+    assert abs((4.0 / 3.0) * math.pi / 3.5 ** 3 - 0.1) < 0.003          # the volume fraction of the lattice
+    d, _ = cKDTree(P).query(P, k=2)
+    assert d[:, 1].min() > 2.0                                          # jitter 0.2 keeps spheres apart
+    assert np.linalg.norm(P, axis=1).max() <= 175.0 + 0.2 * math.sqrt(3)
+    assert np.array_equal(P, hh_synth.lattice_sphere(175.0, 3.5))       # seeded
+    D = hh_synth.two_drops()
+    assert len(D) == 1046610
+    assert np.allclose(D[:523305].mean(0), [0, 0, 525.0], atol=0.05) and np.allclose(D[523305:].mean(0), 0, atol=0.05)
+
+
+def test_lattice_subset_fixed_domain():
+    P = hh_synth.lattice_cube(10, 3.5)
+    assert len(P) == 1000 and np.all(P > -0.21) and np.all(P < 9 * 3.5 + 0.21)
+    S = hh_synth.lattice_subset(300, n_side=10, subset_seed=3)
+    assert len(S) == 300 and len(np.unique(S, axis=0)) == 300
+    assert len({tuple(r) for r in S} & {tuple(r) for r in P}) == 300  # rows of the lattice, in lattice order
+    assert not np.array_equal(S, hh_synth.lattice_subset(300, n_side=10, subset_seed=4))
+
+
+def test_filament_sphere_layout():
+    # the paper's filament suspension, scaled down: chains straight with bead
+    # spacing r_b inside R_in, free particles in the shell, gaps >= 2.1
+    n_fil, beads, n_free = 60, 21, 1260
+    X, r_in, r_out = hh_synth.filament_sphere(n_fil, beads, 3.0, n_free, seed=5)
+    assert X.shape == (n_fil * beads + n_free, 3)
+    assert r_out == pytest.approx(4 * 10 ** (1 / 3) * 20 * 3.0) and r_in == pytest.approx(0.5 ** (1 / 3) * r_out)
+    C = X[:n_fil * beads].reshape(n_fil, beads, 3)
+    seg = np.diff(C, axis=1)
+    assert np.allclose(np.linalg.norm(seg, axis=2), 3.0)
+    t = seg / 3.0
+    assert np.allclose(np.einsum("cbi,cbi->cb", t[:, 1:], t[:, :-1]), 1.0)       # straight
+    assert np.linalg.norm(C, axis=2).max() <= r_in + 1e-9
+    rf = np.linalg.norm(X[n_fil * beads:], axis=1)
+    assert rf.min() >= r_in - 1e-9 and rf.max() <= r_out + 1e-9
+    d, i = cKDTree(X).query(X, k=2)
+    assert d[:, 1].min() >= 2.1 - 1e-9
