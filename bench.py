@@ -63,6 +63,11 @@ partial velocities inside the timed step.
   filsphere    Section 4.3's filament suspension (5120 chains x 21 beads +
                107,520 free particles; k_t 20, k_b 50, dt 0.002, zeta 0.02,
                C_leaf 50), the same way
+  latsub       Section 4.1's fixed-domain scenario: random subsets of one
+               perturbed 100^3 lattice; per N the error of the BF16
+               prediction and of the stored FP32 H-matrix before / after the
+               SVD recompression of its factors, with their bytes and apply
+               times
   peaks        throughput of the units the pair-kernel MLP leans on (MUFU
                ex2 / rcp / tanh, FP32 and FP64 FMA, the epilogue SiLU), with
                the SM clock sampled meanwhile
@@ -738,6 +743,55 @@ def run_workload(args):
                      "rel_err_ci95": rel_err_ci95(Ud, Uh[rows] - a1 * Fh[rows]),
                      "gpu_launches": launches,
                      "clocks": clocks})
+    elif args.workload == "latsub":
+        # Section 4.1's fixed-domain scenario: random subsets of one perturbed 100^3 lattice (spacing 3.5),
+        # so the concentration grows with N.  Per N: eps_r of the fused BF16 prediction and of the stored
+        # FP32 H-matrix before and after the SVD recompression of its factors (eps_rc = zeta), against
+        # 64 exact dense rows; the factor bytes and the low-rank apply's device time before and after
+        rows_n = 64
+        for n in [int(v) for v in args.latsub_n.split(",")]:
+            X = hh_synth.lattice_subset(n, n_side=100, subset_seed=n)
+            F = hh_synth.forces(n, 1)
+            Xd, Fd = torch.as_tensor(X).cuda(), torch.as_tensor(F).cuda()
+            rows = np.sort(np.random.default_rng(n).choice(n, min(rows_n, n), replace=False))
+            Ud = oracle.dense_matvec(X, F, kern, rows=rows, with_self=False)
+            pb = hh.Params(leaf_size=args.leaf, eps=args.eps, precision="bf16")
+            Ub = ctx.predict(Xd, Fd, pb).cpu().numpy()
+            rec = {"workload": "lattice_subset_fixed_domain_100^3_spacing3.5", "n": n,
+                   "phi": n * (4.0 / 3.0) * np.pi / (100 * 3.5) ** 3, "leaf_size": args.leaf, "eps": args.eps,
+                   "rel_err_bf16_predict": float(oracle.rel_error(Ud, Ub[rows] - a1 * F[rows]))}
+            try:
+                p32 = hh.Params(leaf_size=args.leaf, eps=args.eps, precision="fp32")
+                t = ctx.build_tree(Xd, p32)
+                b = ctx.partition(t, p32)
+                h = ctx.aca(t, b, p32)
+                nf = h.factor_count()
+                def apply_ms():
+                    ts = []
+                    for _ in range(5):
+                        U = ctx.matvec(h, Fd)
+                        ts.append(ctx.stats()["t_apply"])
+                    return U.cpu().numpy(), float(np.median(ts))
+                U0, ms0 = apply_ms()
+                t0 = time.perf_counter()
+                h.recompress(args.eps)
+                t_rc = time.perf_counter() - t0
+                sr, so, _ = h.export_recompressed()
+                U1, ms1 = apply_ms()
+                rec.update({"factor_bytes_aca": 4 * 9 * nf, "factor_bytes_svd": 4 * int(so[-1]),
+                            "byte_ratio": int(so[-1]) / max(1, 9 * nf),
+                            "apply_ms_aca": ms0, "apply_ms_svd": ms1,
+                            "apply_gbs_aca": 4 * 9 * nf / (ms0 * 1e6), "apply_gbs_svd": 4 * int(so[-1]) / (ms1 * 1e6),
+                            "recompress_s": t_rc,
+                            "rel_err_fp32_stored": float(oracle.rel_error(Ud, U0[rows] - a1 * F[rows])),
+                            "rel_err_fp32_recompressed": float(oracle.rel_error(Ud, U1[rows] - a1 * F[rows]))})
+                del h, b, t
+            except hh.HHError as e:
+                rec["stored_factors"] = f"skipped: {e}"
+            print(json.dumps(dict(line, metric="relative error and apply bytes, fixed-domain lattice subsets",
+                                  value=rec["rel_err_bf16_predict"], unit="eps_r", higher_is_better=False,
+                                  config=rec)), flush=True)
+        return
     elif args.workload in ("twodrop", "filsphere"):
         # Section 4.3's time-stepped runs: explicit Euler steps through hh_simulate (forces, prediction and
         # update on the GPU; positions copied to the host every --dump-every steps, written as .npy files
@@ -812,6 +866,8 @@ def main():
                     help="memory budget of the BF16 ACA's active blocks in MB (0 = the library default)")
     ap.add_argument("--profile", action="store_true",
                     help="run the warm-up and timed predictions only and print their stage times (for ncu runs)")
+    ap.add_argument("--latsub-n", default="8000,27000,64000,125000,216000",
+                    help="latsub: the subset sizes of the 100^3 lattice")
     ap.add_argument("--dump-every", type=int, default=0,
                     help="twodrop / filsphere: copy the positions to the host every this many steps")
     ap.add_argument("--dump-dir", default=None, help="twodrop / filsphere: write the position dumps here (.npy)")
@@ -819,7 +875,7 @@ def main():
                     help="keep the raw nvidia-smi clock samples of the timed region in this file")
     ap.add_argument("--workload", default="cube1m",
                     choices=["cube1m", "batch64", "grad200k", "cube10m", "shortrange1m", "train", "filament1m", "peaks",
-                             "c2sweep", "twodrop", "filsphere"],
+                             "c2sweep", "twodrop", "filsphere", "latsub"],
                     help="cube1m is the headline; the others measure further configurations")
     args = ap.parse_args()
     if args.clocks_csv:

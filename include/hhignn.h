@@ -149,7 +149,9 @@ hh_status hh_aca(hh_ctx *ctx, const hh_tree *tree, const hh_blocks *blocks, cons
 /* U_dev = alpha_1 F + M_H F (transpose = 0) or alpha_1 F + M_H^T F
  * (transpose = 1), FP64 [N, 3] in the caller's particle order.  Inadmissible
  * blocks are recomputed from the pair kernel on every call; admissible
- * blocks use the stored factors.  Synchronises once (work-list sizes). */
+ * blocks use the stored factors (the recompressed ones after hh_recompress).
+ * Synchronises once (work-list sizes).  hh_stats' t_apply then holds the
+ * low-rank apply's device time (CUDA events, read when hh_stats is called). */
 hh_status hh_matvec(hh_ctx *ctx, const hh_hmat *h, const double *F_dev, double *U_dev, int transpose,
                     void *stream);
 
@@ -437,6 +439,29 @@ hh_status hh_filament_step(hh_ctx *ctx, double *X_dev, int64_t n_chains, int32_t
 hh_status hh_simulate(hh_ctx *ctx, double *X_dev, int64_t n_chains, int32_t beads, int64_t n_free,
                       const hh_filament_params *fp, const hh_params *p, double dt, int32_t n_steps,
                       int32_t dump_every, double *X_dump_host, double *t_step_ms, void *stream);
+
+/* Recompression of the stored ACA factors by truncated SVD (the paper
+ * stores the ACA factors as they come; this lowers the bytes the low-rank
+ * apply reads).  Per admissible block, M = sum_k C_k Q_k in scalar form
+ * (3|tau| x 3|sigma|, scalar rank <= 3 rank) is replaced by U V with U
+ * (3|tau| x r), V (r x 3|sigma|) and r the smallest rank whose discarded
+ * singular values satisfy sum_{i>=r} s_i^2 <= eps_rc^2 sum_i s_i^2, so
+ * ||M - U V||_F <= eps_rc ||M||_F (Eckart-Young; the singular values come
+ * from FP64 Jacobi eigendecompositions of the factors' Gram matrices and a
+ * 3 rank x 3 rank core, values below ~3e-8 of the largest count as zero).
+ * U and V are stored in h's real type; the ACA factors are freed.  h must
+ * hold factors (not HH_FLAG_PIVOTS_ONLY) and max_rank <= 64; eps_rc in
+ * [0, 1).  hh_matvec then applies U V; hh_matvec_backward treats h as
+ * pivots-only (rebuilds its FP64 factors).  Synchronises. */
+hh_status hh_recompress(hh_ctx *ctx, hh_hmat *h, double eps_rc, void *stream);
+
+/* Copies the recompressed factors to host buffers (NULL pointers skipped):
+ * srank[nG] kept ranks, sofs[nG+1] offsets in reals, sfac[n_sfac] (block b
+ * at sofs[b]: U row-major [r][3|tau|] -- row rho holds column rho of U --
+ * then V [r][3|sigma|]; entry 3m + u of a U row is particle m, component u).
+ * HH_ERR_ARG if h was not recompressed.  Synchronises the device. */
+hh_status hh_export_recompressed(const hh_hmat *h, int32_t *srank, int64_t *sofs, void *sfac, int64_t *n_sfac,
+                                 int32_t *real_bytes);
 
 /* Test hooks for the failure paths (the paper has no counterpart).
  *

@@ -40,6 +40,10 @@ PINS = {
     "filament_forces": "central differences of filament_energy; the two-bead spring; zero net internal force and "
                        "torque per chain; straight chains at rest length feel gravity only",
     "euler_step": "composition of filament_forces, hmatvec and x + dt U (each pinned)",
+    "simulate": "two identical spheres under RPY sediment together at the closed-form velocity; dt = 0 keeps X; "
+                "one step equals euler_step",
+    "recompress": "matrices of prescribed singular values: the kept rank and the error are the Eckart-Young "
+                  "ones; exact for rank-deficient factors; error <= eps_rc ||M||_F on ACA blocks",
 }
 
 
@@ -406,3 +410,35 @@ def simulate(X, n_chains, beads, kernel, dt, n_steps, dump_every=1, leaf=32, eta
         if dump_every and step % dump_every == 0:
             dumps.append(X.copy())
     return dumps
+
+
+def block_matrix(C, Q):
+    """The scalar form M = sum_k C_k Q_k (3c x 3q) of a block's 3x3 factors,
+    C [l, c, 3, 3] and Q [l, q, 3, 3] as aca_block returns them: entry
+    (3m + a, 3n + b) = sum_k sum_x C_k(m)[a][x] Q_k(n)[x][b]."""
+    C = _f64(C); Q = _f64(Q)
+    l, c = C.shape[:2]
+    q = Q.shape[1]
+    if l == 0:
+        return np.zeros((3 * c, 3 * q))
+    Cs = C.transpose(1, 2, 0, 3).reshape(3 * c, 3 * l)      # row 3m + a, column 3k + x
+    Qs = Q.transpose(0, 2, 1, 3).reshape(3 * l, 3 * q)      # row 3k + x, column 3n + b
+    return Cs @ Qs
+
+
+def recompress(C, Q, eps_rc):
+    """Truncated SVD of a block's ACA approximant (the paper stores the ACA
+    factors unchanged; this is the textbook best rank-r approximation,
+    Eckart-Young): with M = block_matrix(C, Q) = sum_i s_i u_i v_i^T, the
+    smallest r with sum_{i >= r} s_i^2 <= eps_rc^2 sum_i s_i^2.  Returns
+    (U [3c, r] = the u_i s_i, V [r, 3q] = the v_i^T, r, s)."""
+    M = block_matrix(C, Q)
+    if M.size == 0:
+        return np.zeros((M.shape[0], 0)), np.zeros((0, M.shape[1])), 0, np.zeros(0)
+    u, s, vt = np.linalg.svd(M, full_matrices=False)
+    tot = float(np.sum(s * s))
+    r, tail = len(s), 0.0
+    while r > 0 and tail + s[r - 1] ** 2 <= eps_rc * eps_rc * tot:
+        tail += s[r - 1] ** 2
+        r -= 1
+    return u[:, :r] * s[:r], vt[:r], r, s

@@ -36,7 +36,7 @@ EXPORTS = [
     "hh_aca_block_apply_noalloc", "hh_eval_pairs", "hh_train_loss_grad", "hh_train_step",
     "hh_set_launch", "hh_get_launch", "hh_autotune", "hh_set_short_range", "hh_short_range",
     "hh_filament_forces", "hh_filament_step", "hh_probe_throughput", "hh_shard_owners",
-    "hh_debug_fail_alloc", "hh_debug_stall_mma_waits", "hh_simulate",
+    "hh_debug_fail_alloc", "hh_debug_stall_mma_waits", "hh_simulate", "hh_recompress", "hh_export_recompressed",
 ]
 
 
@@ -116,6 +116,8 @@ def lib():
             "hh_probe_throughput": (st, [_P, i32, ctypes.c_int64, _P, _P]),
             "hh_shard_owners": (st, [_P, i32, _P, _P]),
             "hh_debug_fail_alloc": (None, [ctypes.c_int64]),
+            "hh_recompress": (st, [_P, _P, ctypes.c_double, _P]),
+            "hh_export_recompressed": (st, [_P, _P, _P, _P, _P, _P]),
             "hh_simulate": (st, [_P, _P, ctypes.c_int64, i32, ctypes.c_int64, _P, _P, ctypes.c_double, i32, i32, _P,
                                  _P, _P]),
             "hh_debug_stall_mma_waits": (st, [_P, ctypes.c_uint32]),
@@ -497,6 +499,31 @@ class HMatrix(_Owned):
         self.ctx._check(lib().hh_export_factors(self._h, fofs.ctypes.data_as(_P), fac.ctypes.data_as(_P), None,
                                                 None), "hh_export_factors")
         return fofs, fac[: 9 * nf.value]
+
+    def factor_count(self) -> int:
+        """Stored factor elements (9 reals each; hh_export_factors' n_factor)."""
+        nf = ctypes.c_int64()
+        self.ctx._check(lib().hh_export_factors(self._h, None, None, ctypes.byref(nf), None), "hh_export_factors")
+        return nf.value
+
+    def recompress(self, eps_rc: float, stream=None):
+        """Truncated-SVD recompression of the stored factors (hh_recompress)."""
+        self.ctx._check(lib().hh_recompress(self.ctx._h, self._h, float(eps_rc), _stream(stream)), "hh_recompress")
+
+    def export_recompressed(self):
+        """(srank [nG], sofs [nG + 1], sfac): block b holds U [r][3c] then V
+        [r][3q] from sofs[b] on (hh_export_recompressed)."""
+        nG = ctypes.c_int64()
+        self.ctx._check(lib().hh_export_aca(self._h, None, None, None, ctypes.byref(nG), None), "hh_export_aca")
+        ns, rb = ctypes.c_int64(), ctypes.c_int32()
+        self.ctx._check(lib().hh_export_recompressed(self._h, None, None, None, ctypes.byref(ns), ctypes.byref(rb)),
+                        "hh_export_recompressed")
+        sr = np.zeros(max(nG.value, 1), np.int32)
+        so = np.zeros(nG.value + 1, np.int64)
+        sf = np.zeros(max(ns.value, 1), np.float64 if rb.value == 8 else np.float32)
+        self.ctx._check(lib().hh_export_recompressed(self._h, sr.ctypes.data_as(_P), so.ctypes.data_as(_P),
+                                                     sf.ctypes.data_as(_P), None, None), "hh_export_recompressed")
+        return sr[:nG.value], so, sf
 
 
 def _width_of(n_theta: int) -> int:

@@ -196,6 +196,7 @@ void free_hmat(hh_hmat* h)
 {
     if (!h) return;
     cudaFree(h->rank); cudaFree(h->pivI); cudaFree(h->pivJ); cudaFree(h->fofs); cudaFree(h->factors);
+    cudaFree(h->srank); cudaFree(h->sofs); cudaFree(h->sfac);
     delete h;
 }
 
@@ -448,7 +449,8 @@ hh_status hh_matvec(hh_ctx* ctx, const hh_hmat* h, const double* F_dev, double* 
     if (!ctx || !h) return HH_ERR_ARG;
     return guarded(ctx, [&]() {
         HH_REQUIRE(F_dev && U_dev, HH_ERR_ARG, "F or U is NULL");
-        HH_REQUIRE(h->factors != nullptr, HH_ERR_ARG, "H-matrix built with HH_FLAG_PIVOTS_ONLY has no factors");
+        HH_REQUIRE(h->factors != nullptr || h->sfac != nullptr, HH_ERR_ARG,
+                   "H-matrix built with HH_FLAG_PIVOTS_ONLY has no factors");
         cudaStream_t s = (cudaStream_t)stream;
         const hh_tree* t = h->tree;
         const hh_blocks* b = h->blocks;
@@ -465,7 +467,11 @@ hh_status hh_matvec(hh_ctx* ctx, const hh_hmat* h, const double* F_dev, double* 
         int64_t* pofs = dev_alloc_t<int64_t>(b->nG + 1, s);
         int64_t total = partial_offsets(t, b, transpose, pofs, s);
         void* part = dev_alloc(rb * 3 * (size_t)(total > 0 ? total : 1), s);
-        lowrank_apply(ctx, h, Fs, part, pofs, transpose, s);
+        HH_CUDA(cudaEventRecord(ctx->kev[6], s));
+        if (h->sfac) recompressed_apply(h, Fs, part, pofs, transpose, s);
+        else lowrank_apply(ctx, h, Fs, part, pofs, transpose, s);
+        HH_CUDA(cudaEventRecord(ctx->kev[7], s));
+        ctx->kev_apply_pending = true;
         int32_t* order = nullptr;
         int64_t* col = nullptr;
         if (transpose) {
@@ -768,7 +774,42 @@ hh_status hh_stats(hh_ctx* ctx, hh_stats_t* out)
 {
     if (!ctx || !out) return HH_ERR_ARG;
     return guarded(ctx, [&]() {
+        if (ctx->kev_apply_pending) {   // the last hh_matvec's low-rank apply
+            float ms = 0.f;
+            HH_CUDA(cudaEventSynchronize(ctx->kev[7]));
+            HH_CUDA(cudaEventElapsedTime(&ms, ctx->kev[6], ctx->kev[7]));
+            ctx->stats.t_apply = ms;
+            ctx->kev_apply_pending = false;
+        }
         *out = ctx->stats;
+        return HH_OK;
+    });
+}
+
+hh_status hh_recompress(hh_ctx* ctx, hh_hmat* h, double eps_rc, void* stream)
+{
+    if (!ctx || !h) return HH_ERR_ARG;
+    return guarded(ctx, [&]() {
+        HH_REQUIRE(h->ctx == ctx, HH_ERR_ARG, "the H-matrix belongs to another context");
+        recompress_factors(ctx, h, eps_rc, (cudaStream_t)stream);
+        return HH_OK;
+    });
+}
+
+hh_status hh_export_recompressed(const hh_hmat* h, int32_t* srank, int64_t* sofs, void* sfac, int64_t* n_sfac,
+                                 int32_t* real_bytes)
+{
+    if (!h) return HH_ERR_ARG;
+    return guarded(h->ctx, [&]() {
+        HH_REQUIRE(h->srank != nullptr, HH_ERR_ARG, "the H-matrix has not been recompressed");
+        HH_CUDA(cudaDeviceSynchronize());
+        const int64_t n = h->blocks->nG;
+        if (srank && n) HH_CUDA(cudaMemcpy(srank, h->srank, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+        if (sofs) HH_CUDA(cudaMemcpy(sofs, h->sofs, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
+        if (sfac && h->n_sfac > 0)
+            HH_CUDA(cudaMemcpy(sfac, h->sfac, (size_t)h->real_bytes * h->n_sfac, cudaMemcpyDeviceToHost));
+        if (n_sfac) *n_sfac = h->n_sfac;
+        if (real_bytes) *real_bytes = h->real_bytes;
         return HH_OK;
     });
 }

@@ -28,6 +28,7 @@ struct hh_ctx {
     cudaEvent_t kev[8] = {};             // around the ACA (0..3) and near (4,5) kernels
     int kev_aca_used = 0;                // ACA kernel event pairs recorded this call
     int kev_near_used = 0;
+    bool kev_apply_pending = false;      // hh_matvec recorded kev[6], kev[7] around its low-rank apply
     unsigned long long launch_base = 0;  // g_hh_launches at the start of the call
     hh_launch_cfg launch{};              // 0 fields: defaults (see resolved_launch)
     cudaStream_t aux = nullptr;          // second stream: CTA-team ACA classes beside the warp teams
@@ -101,6 +102,12 @@ struct hh_hmat {
     void* factors = nullptr;   // per block: C [rank][9][c] then Q [rank][9][q]
     int64_t n_factor = 0;      // total elements
     int real_bytes = 4;
+    // after hh_recompress (the ACA factors are then freed): per block the kept
+    // scalar rank, the offsets (reals) and U [r][3c] then V [r][3q]
+    int32_t* srank = nullptr;
+    int64_t* sofs = nullptr;
+    void* sfac = nullptr;
+    int64_t n_sfac = 0;
 };
 
 // --- primitives (hh_prims.cu) ------------------------------------------------
@@ -283,6 +290,12 @@ void accumulate_end(const hh_tree* t, const double* Us, double* U, cudaStream_t 
 // receives each group's first offset and, last, the total.  Synchronises.
 std::vector<std::pair<int64_t, int64_t>> block_groups(const hh_blocks* b, const int64_t* pofs, int64_t total,
                                                       int64_t cap, std::vector<int64_t>* pofs_at, cudaStream_t s);
+
+// SVD recompression of the stored factors (hh_recompress.cu): replaces
+// h->factors by the recompressed U, V (synchronises); and their apply.
+void recompress_factors(hh_ctx* ctx, hh_hmat* h, double eps_rc, cudaStream_t s);
+void recompressed_apply(const hh_hmat* h, const double* Fs, void* part, const int64_t* pofs, int transpose,
+                        cudaStream_t s);
 
 // Partial-output offsets: pofs[b] = sum_{b' < b} |target(b')| (or source if
 // transpose); returns the total (synchronises).

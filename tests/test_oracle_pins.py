@@ -521,3 +521,57 @@ def test_dense_matvec_multi_equals_single():
     for f in range(5):
         assert np.array_equal(Um[f], oracle.dense_matvec(X, Fs[f], k, rows=rows, with_self=False))
     assert np.array_equal(oracle.dense_matvec_multi(X, Fs[:1], k)[0], oracle.dense_matvec(X, Fs[0], k))
+
+
+# --------------------------------------------------------------------------
+# SVD recompression of a block's factors
+# --------------------------------------------------------------------------
+def _factors_of(M, c, q):
+    """3x3 factors C [l, c, 3, 3], Q [l, q, 3, 3] whose block_matrix is M
+    (3c x 3q), with l = 3c / 3 = c steps of an exact split M = I M."""
+    l = c
+    Cs = np.eye(3 * c)
+    C = Cs.reshape(c, 3, l, 3).transpose(2, 0, 1, 3)
+    Q = M.reshape(l, 3, q, 3).transpose(0, 2, 1, 3)
+    return C, Q
+
+
+def test_recompress_prescribed_singular_values():
+    # M = P diag(s) R^T with orthonormal P, R: the kept rank is the one the
+    # tail rule gives and the error equals the discarded tail (Eckart-Young)
+    rng = np.random.default_rng(3)
+    c, q = 6, 5
+    P, _ = np.linalg.qr(rng.standard_normal((3 * c, 15)))
+    R, _ = np.linalg.qr(rng.standard_normal((3 * q, 15)))
+    s = 10.0 ** -np.arange(15, dtype=float) * 3.0
+    M = (P * s) @ R.T
+    C, Q = _factors_of(M, c, q)
+    assert np.allclose(oracle.block_matrix(C, Q), M, rtol=0, atol=1e-14)
+    # tail(r) / ||M|| = 10^-r exactly for this geometric spectrum
+    for eps, r_want in ((2e-3, 3), (5e-6, 6), (0.0, 15)):
+        U, V, r, sv = oracle.recompress(C, Q, eps)
+        tail = np.sqrt(np.sum(s[r_want:] ** 2))
+        assert r == r_want and U.shape == (3 * c, r) and V.shape == (r, 3 * q)
+        assert np.allclose(sv[:15], s, rtol=1e-10)
+        assert abs(np.linalg.norm(M - U @ V) - tail) <= 1e-12 * np.linalg.norm(M) + 1e-9 * tail
+        assert tail <= eps * np.linalg.norm(M) + 1e-15
+
+
+def test_recompress_aca_blocks():
+    # on ACA blocks of the MLP kernel: rank <= 3 l, error within eps_rc, and
+    # the scalar rank is below the 3 l the 3x3 steps give
+    X = hh_synth.rsa_cube(1500, 0.1, seed=12)
+    k = oracle.PairKernel("mlp", hh_synth.mlp_params(32, 7), 32)
+    t = oracle.build_tree(X, 32)
+    G, _ = oracle.partition(t, 32, 1.0)
+    fewer = 0
+    for tau, sig in G[:: max(1, len(G) // 40)]:
+        t0, c, s0, q = int(t.begin[tau]), int(t.size(tau)), int(t.begin[sig]), int(t.size(sig))
+        a = oracle.aca_block(k, t.Xs, t0, c, s0, q, 1e-6, 48, 0)
+        l = a["rank"]
+        M = oracle.block_matrix(a["C"], a["Q"])
+        U, V, r, _ = oracle.recompress(a["C"], a["Q"], 1e-4)
+        assert r <= 3 * l
+        assert np.linalg.norm(M - U @ V) <= 1e-4 * np.linalg.norm(M) * (1 + 1e-12)
+        fewer += r < 3 * l
+    assert fewer > 0
