@@ -164,11 +164,12 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm)}
 
 
-# DRAM bytes (read + write) per pair-kernel query of the BF16 ACA kernels, from
-# one ncu capture of every k_aca_tc launch of a prediction at N = 100,000
-# (profiles/k_aca_tc_bf16_n100k.md); the traffic of a launch is taken as
-# proportional to its queries.
-ACA_TC_DRAM_BYTES_PER_QUERY = 418.0
+# DRAM bytes (read + write) per pair-kernel query of the BF16 ACA, from one
+# ncu capture of every ACA launch (k_aca_tc warp and CTA teams, k_round_*) of
+# a prediction at N = 100,000 (profiles/k_aca_tc_warp_bf16_n100k.md):
+# 379.4 GB for 906,080,506 queries.  The traffic of a prediction is taken as
+# proportional to its queries (the per-block working set does not grow with N).
+ACA_TC_DRAM_BYTES_PER_QUERY = 418.8
 
 
 def aca_traffic(queries):
