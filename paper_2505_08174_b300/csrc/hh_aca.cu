@@ -139,15 +139,25 @@ __device__ void aca_block(const AcaArgs<R>& A, const Team& tm, S& sm, const R* t
                 double P[9], Pi[9];
 #pragma unroll
                 for (int e = 0; e < 9; ++e) P[e] = (double)Cs[((int64_t)k * 9 + e) * c + bi];
-                double det = inv3d(P, Pi);
-                double rc = det != 0.0 ? 1.0 / sqrt(fro2(P) * fro2(Pi)) : 0.0;
-                int bad = !(det != 0.0) || !(rc >= 1e-10);
+                int bad;
+                if constexpr (sizeof(R) == 4) {   // FP32 residuals: noise floor (inv3_floor)
+                    if (k == 0) sm.pscale = sqrt(fro2(P));
+                    double det;
+                    const int kept = inv3_floor(P, PIVOT_FLOOR_FP32 * sm.pscale, Pi, &det);
+                    const double rc = kept == 3 ? 1.0 / sqrt(fro2(P) * fro2(Pi)) : 1.0;
+                    bad = kept == 0 ? 2 : (!(rc >= 1e-10) ? 1 : 0);
+                } else {
+                    double det = inv3d(P, Pi);
+                    double rc = det != 0.0 ? 1.0 / sqrt(fro2(P) * fro2(Pi)) : 0.0;
+                    bad = !(det != 0.0) || !(rc >= 1e-10);
+                }
                 sm.flag = bad;
                 if (!bad)
 #pragma unroll
                     for (int e = 0; e < 9; ++e) sm.Pi[e] = (R)Pi[e];
             }
             tm.sync();
+            if (sm.flag == 2) { done = true; break; }   // the pivot element is rounding noise
             if (sm.flag) {
                 double bd = 0.0;
                 int bdi = -1;

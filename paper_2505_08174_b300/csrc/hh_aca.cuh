@@ -59,6 +59,7 @@ struct alignas(16) TeamSmem {
     double rv[8];
     int ri[8];
     int flag, stop;
+    double pscale;         // Frobenius norm of the block's first pivot element
 };
 
 __device__ __forceinline__ uint64_t splitmix_once(uint64_t x)

@@ -69,6 +69,7 @@ struct Slots {
     int32_t* jb;       // j_k
     int32_t* pivst;    // pivot status after a column pass (k_round_pivots)
     double* lam2;
+    double* pscale;    // Frobenius norm of the block's first pivot element
     unsigned long long* key;   // argmax of the running pass: (value bits << 32) | ~index
     float* Pi;         // [S][9] pivot inverse of the current column
     float* piv;        // [S][9 MR]: Q_p(j_k) (for COL) or C_p(i_k) (for ROW), p < k
@@ -469,9 +470,12 @@ __global__ void __launch_bounds__(128) k_round_pivots(RoundArgs R)
     double P[9], Pi[9];
 #pragma unroll
     for (int e = 0; e < 9; ++e) P[e] = (double)Cs[((int64_t)k * 9 + e) * c + bi];
-    const double det = inv3d(P, Pi);
-    const double rc = det != 0.0 ? 1.0 / sqrt(fro2(P) * fro2(Pi)) : 0.0;
-    if (!(det != 0.0) || !(rc >= 1e-10)) { S.pivst[s] = 2; return; }
+    if (k == 0) S.pscale[s] = sqrt(fro2(P));
+    double det;
+    const int kept = inv3_floor(P, PIVOT_FLOOR_BF16 * S.pscale[s], Pi, &det);
+    if (kept == 0) { S.pivst[s] = 0; return; }   // the pivot element is rounding noise: the block ends
+    const double rc = kept == 3 ? 1.0 / sqrt(fro2(P) * fro2(Pi)) : 1.0;
+    if (!(rc >= 1e-10)) { S.pivst[s] = 2; return; }
 #pragma unroll
     for (int e = 0; e < 9; ++e) S.Pi[(int64_t)s * 9 + e] = (float)Pi[e];
     S.ib[s] = bi;
@@ -791,7 +795,7 @@ int64_t slot_stride_bound(int64_t M, int64_t MR)
 size_t slot_state_bytes(int64_t S, int MR)
 {
     auto r = [](int64_t b) { return (size_t)((b + 255) / 256 * 256); };
-    return 11 * r(4 * S) + 2 * r(8 * S) + r(4 * 9 * S) + r(4 * 9 * MR * S) + r(4 * 3 * MR * S);
+    return 11 * r(4 * S) + 3 * r(8 * S) + r(4 * 9 * S) + r(4 * 9 * MR * S) + r(4 * 3 * MR * S);
 }
 
 }  // namespace
@@ -870,6 +874,7 @@ void aca_rounds_run(hh_ctx* ctx, const hh_tree* t, const hh_blocks* bl, const hh
         S.k = (int32_t*)take(4 * Sa); S.phase = (int32_t*)take(4 * Sa); S.ib = (int32_t*)take(4 * Sa);
         S.jb = (int32_t*)take(4 * Sa); S.pivst = (int32_t*)take(4 * Sa);
         S.lam2 = (double*)take(8 * Sa);
+        S.pscale = (double*)take(8 * Sa);
         S.key = (unsigned long long*)take(8 * Sa);
         S.Pi = (float*)take(4 * 9 * Sa);
         S.piv = (float*)take(4 * 9 * MR * Sa);

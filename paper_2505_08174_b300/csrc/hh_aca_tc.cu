@@ -299,15 +299,18 @@ __global__ void __launch_bounds__(TC_T, 4) k_aca_tc(AcaArgs<float> A, const floa
                 double P[9], Pi[9];
 #pragma unroll
                 for (int e = 0; e < 9; ++e) P[e] = (double)Cs[((int64_t)k * 9 + e) * c + bi];
-                const double det = inv3d(P, Pi);
-                const double rc = det != 0.0 ? 1.0 / sqrt(fro2(P) * fro2(Pi)) : 0.0;
-                const int bad = !(det != 0.0) || !(rc >= 1e-10);
+                if (k == 0) sm.pscale = sqrt(fro2(P));
+                double det;
+                const int kept = inv3_floor(P, PIVOT_FLOOR_BF16 * sm.pscale, Pi, &det);
+                const double rc = kept == 3 ? 1.0 / sqrt(fro2(P) * fro2(Pi)) : 1.0;
+                const int bad = kept == 0 ? 2 : (!(rc >= 1e-10) ? 1 : 0);
                 sm.flag = bad;
                 if (!bad)
 #pragma unroll
                     for (int e = 0; e < 9; ++e) sm.Pi[e] = (float)Pi[e];
             }
             tm.sync();
+            if (sm.flag == 2) { finish(k, false); continue; }   // the pivot element is rounding noise
             if (sm.flag) {
                 double bd = 0.0;
                 int bdi = -1;

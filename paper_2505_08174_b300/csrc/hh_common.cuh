@@ -95,6 +95,48 @@ __device__ __forceinline__ double inv3d(const double* P, double* Pi)
     return det;
 }
 
+// Pivot element inverse when the residuals are formed in FP32 (the FP32 and
+// BF16 block ACA).  Below its noise floor tau -- the rounding noise of the
+// residual entries, or the BF16 MLP's entry error -- a singular value of
+// the pivot element P is noise, and inverting it would amplify the noise of
+// the whole column into the new rank term (such blocks then never meet
+// Eq. 10 and run to max_rank).  So:
+//  * 1 / ||P^-1||_F (a lower bound of the smallest singular value) above
+//    tau: Pi = P^-1 from the adjugate, as in the FP64 path (*det = det P);
+//  * ||P||_F (an upper bound of the largest) at or below tau: the pivot is
+//    noise (returns 0);
+//  * otherwise the damped inverse Pi = (P^T P + tau^2 I)^-1 P^T, which maps
+//    a singular value s to s / (s^2 + tau^2): 1/s for s >> tau, ~0 for
+//    s << tau (returns 1; *det = 0).
+__device__ __forceinline__ int inv3_floor(const double* P, double tau, double* Pi, double* det)
+{
+    *det = inv3d(P, Pi);
+    const double f = fro2(Pi);
+    if (*det != 0.0 && f < 1e300 && 1.0 / sqrt(f) > tau) return 3;
+    *det = 0.0;
+    if (!(fro2(P) > tau * tau)) return 0;
+    double A[9], Ai[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            A[3 * i + j] = P[i] * P[j] + P[3 + i] * P[3 + j] + P[6 + i] * P[6 + j] + (i == j ? tau * tau : 0.0);
+    inv3d(A, Ai);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)   // (A^-1 P^T)[i][j] = sum_c A^-1[i][c] P[j][c]
+            Pi[3 * i + j] = Ai[3 * i] * P[3 * j] + Ai[3 * i + 1] * P[3 * j + 1] + Ai[3 * i + 2] * P[3 * j + 2];
+    return 1;
+}
+
+// Noise floors of inv3_floor relative to the Frobenius norm of a block's
+// first pivot element: FP32 residual entries carry ~ k u |G| rounding noise
+// (u = 2^-24, k <= 48 terms: at most 2.9e-6), below 2^-17 = 128 u; the BF16
+// hi/lo MLP's entries carry up to ~2^-16 relative error, below 2^-15.
+constexpr double PIVOT_FLOOR_FP32 = 1.0 / 131072.0;
+constexpr double PIVOT_FLOOR_BF16 = 1.0 / 32768.0;
+
 // ---------------------------------------------------------------------------
 // Pair kernels.  r = x_target - x_source (non-zero).  K is row-major 3x3.
 // ---------------------------------------------------------------------------

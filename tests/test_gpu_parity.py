@@ -181,8 +181,12 @@ def test_predict_against_dense(ctx, eps, prec):
         Ud = oracle.dense_matvec(X, F, ks, with_self=True)
         errs.append(oracle.rel_error(Ud - a1 * F, U - a1 * F))
         if s == 0 and prec == "fp32":
+            # the FP32 path does not invert singular values of a pivot element
+            # below the noise floor of its FP32 residuals (2^-17 of the first
+            # pivot's norm), where the FP64 oracle inverts them: a few terms
+            # differ at that level (observed 2.9e-5 at zeta = 1e-3)
             Uo, _ = oracle.hmatvec(X, F, ks, leaf=32, eta=1.0, eps=eps, max_rank=48)
-            assert oracle.rel_error(Uo, U) < 2e-5
+            assert oracle.rel_error(Uo, U) < 5e-5
     assert np.mean(errs) <= (eps if prec == "fp64" else max(eps, FP32_FLOOR))
 
 
@@ -443,3 +447,30 @@ def test_bf16_rounds_independent_of_budget_and_j1_rule_1(ctx):
     U1 = ctx.predict(cuda(Xh), cuda(Fh), p).cpu().numpy()
     Uo, _ = oracle.hmatvec(Xh, Fh, kern(), leaf=32, eta=1.0, eps=1e-4, max_rank=48, j1_rule=1, seed=5)
     assert oracle.rel_error(Uo, U1) < 1e-4
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6])
+def test_low_precision_rank_loops_stop_at_their_noise_floor(ctx, eps):
+    # FP32 residuals: pivot elements whose singular values sit at the rounding
+    # noise of the residual entries are not inverted (damped inverse), so a
+    # block's rank loop does not fit amplified noise and run to max_rank.
+    # Without it, at N = 30k RPY the FP32 error was 5x the FP64 one at
+    # zeta = 1e-4 and flat near 2.6e-4 at zeta = 1e-6
+    n = 30000
+    X = hh_synth.rsa_cube(n, 0.1, seed=21)
+    F = hh_synth.forces(n, 1)
+    rows = np.sort(np.random.default_rng(2).choice(n, 256, replace=False))
+    Ud = oracle.dense_matvec(X, F, kern("rpy"), rows=rows, with_self=False)
+    a1 = oracle.self_mobility()
+    err = {}
+    for prec in ("fp64", "fp32"):
+        p = hh.Params(precision=prec, eps=eps, leaf_size=64, kernel="rpy")
+        U = ctx.predict(cuda(X), cuda(F), p).cpu().numpy()
+        err[prec] = oracle.rel_error(Ud, U[rows] - a1 * F[rows])
+        if prec == "fp32":
+            t = ctx.build_tree(cuda(X), p)
+            b = ctx.partition(t, p)
+            h = ctx.aca(t, b, hh.Params(precision=prec, eps=eps, leaf_size=64, kernel="rpy", pivots_only=True))
+            ranks, _, _ = h.export()
+            assert np.mean(ranks == 48) < 0.01, np.mean(ranks == 48)
+    assert err["fp32"] <= 2.0 * err["fp64"] + 2e-5, err
