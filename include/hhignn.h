@@ -350,7 +350,7 @@ hh_status hh_stats(hh_ctx *ctx, hh_stats_t *out);
  *                  (256-thread FP32 / FP64 kernel) or 4 (128-thread BF16
  *                  tensor-core kernel)
  *   near_cps       CTAs per SM of the tensor-core near-field kernel, 1..8,
- *                  default 4
+ *                  default 5 (its 96 registers and shared tiles fit five)
  *   rounds_min_cq  (HH_BF16) admissible blocks with c + q above this value go
  *                  through the round-based ACA (every block of a size class
  *                  advancing one phase per round, its rows spread over the
@@ -377,7 +377,7 @@ hh_status hh_get_launch(hh_ctx *ctx, hh_launch_cfg *cfg);
  * shapes and keeps the fastest on ctx (also written to *best when not NULL).
  * Coordinate descent from ctx's current shape: each field in turn is swept
  * over a fixed candidate list (small_max 128 / 256 / 512, aca_small_cps 1..4,
- * aca_large_cps 1 / 2 / 4, near_cps 2 / 4 / 8, rounds_min_cq 2048 / 4096 /
+ * aca_large_cps 1 / 2 / 4, near_cps 2 / 4 / 5 / 8, rounds_min_cq 2048 / 4096 /
  * 16384) with the others held, and the
  * value of the smallest median time over reps (>= 1) predictions is kept.
  * Results do not depend on the launch shape beyond FP rounding order of the

@@ -941,13 +941,13 @@ hh_status hh_autotune(hh_ctx* ctx, const double* X_dev, const int64_t* offsets, 
     static const int32_t cand_small_max[] = {128, 256, 512};
     static const int32_t cand_small_cps[] = {1, 2, 3, 4};
     static const int32_t cand_large_cps[] = {1, 2, 4};
-    static const int32_t cand_near_cps[] = {2, 4, 8};
+    static const int32_t cand_near_cps[] = {2, 4, 5, 8};
     static const int32_t cand_rounds[] = {2048, 4096, 16384};
     struct Field { int32_t hh_launch_cfg::*f; const int32_t* v; int nv; };
     const Field fields[] = {{&hh_launch_cfg::small_max, cand_small_max, 3},
                             {&hh_launch_cfg::aca_small_cps, cand_small_cps, 4},
                             {&hh_launch_cfg::aca_large_cps, cand_large_cps, 3},
-                            {&hh_launch_cfg::near_cps, cand_near_cps, 3},
+                            {&hh_launch_cfg::near_cps, cand_near_cps, 4},
                             {&hh_launch_cfg::rounds_min_cq, cand_rounds, 3}};
     for (const Field& fd : fields) {
         for (int i = 0; i < fd.nv && st == HH_OK; ++i) {

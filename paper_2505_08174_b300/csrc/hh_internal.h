@@ -54,7 +54,7 @@ inline hh_launch_cfg resolved_launch(const hh_ctx* ctx, bool tc)
     if (c.small_max <= 0) c.small_max = 512;
     if (c.aca_small_cps <= 0) c.aca_small_cps = 4;
     if (c.aca_large_cps <= 0) c.aca_large_cps = tc ? 4 : 2;
-    if (c.near_cps <= 0) c.near_cps = 4;
+    if (c.near_cps <= 0) c.near_cps = 5;
     if (c.rounds_min_cq <= 0) c.rounds_min_cq = 4096;
     return c;
 }
