@@ -166,7 +166,7 @@ class ClockSampler:
 
 # DRAM bytes (read + write) per pair-kernel query of the BF16 ACA, from one
 # ncu capture of every ACA launch (k_aca_tc warp and CTA teams, k_round_*) of
-# a prediction at N = 100,000 (profiles/k_aca_tc_warp_bf16_n100k.md):
+# a prediction at N = 100,000 (the ACA capture kept under profiles/):
 # 278.9 GB for 809,273,239 queries.  The traffic of a prediction is taken as
 # proportional to its queries (the per-block working set does not grow with N).
 ACA_TC_DRAM_BYTES_PER_QUERY = 344.6
