@@ -555,7 +555,7 @@ def run_workload(args):
             refs[kind] = oracle.dense_matvec(X, F, oracle.PairKernel(kind, th64, 64), rows=rows, with_self=False)
             refs[kind + "_s"] = time.perf_counter() - t0
         for kind in ("mlp", "rpy"):
-            for prec in ("fp64", "fp32", "bf16"):
+            for prec in args.c2_precisions.split(","):
                 if kind == "rpy" and prec == "bf16":
                     continue
                 for eta in (0.7, 1.0, 1.5):
@@ -867,6 +867,8 @@ def main():
                     help="memory budget of the BF16 ACA's active blocks in MB (0 = the library default)")
     ap.add_argument("--profile", action="store_true",
                     help="run the warm-up and timed predictions only and print their stage times (for ncu runs)")
+    ap.add_argument("--c2-precisions", default="fp64,fp32,bf16",
+                    help="c2sweep: the precisions swept (comma-separated)")
     ap.add_argument("--latsub-n", default="8000,27000,64000,125000,216000",
                     help="latsub: the subset sizes of the 100^3 lattice")
     ap.add_argument("--dump-every", type=int, default=0,
